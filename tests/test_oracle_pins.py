@@ -1,0 +1,426 @@
+"""Pins of the CPU oracle against things other than itself.
+
+Each test checks one oracle function against brute force, a closed form, an
+invariant the paper states, or a third-party implementation, chosen so that a
+dropped term, a wrong sign or index or a transposed operand fails one of them.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from oracle import philox
+from paper_2002_06960_gb300 import inputs
+
+from thirdparty import aten_words
+
+f64 = torch.float64
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- Philox ----
+
+@pytest.mark.parametrize("seed,ctr", [
+    (0, (0, 0, 0, 0)),
+    (2 ** 64 - 1, (0xFFFFFFFF,) * 4),
+    (123456789012345, (5, 9, 7, 3)),
+    (0xDEADBEEF, (1 << 31, 17, 0, 4)),
+])
+def test_philox_words_match_aten(seed, ctr):
+    mine = philox.philox4x32_10(np.array([ctr], dtype=np.uint64), philox.seed_key(seed))[0]
+    assert np.array_equal(mine, aten_words(seed, ctr))
+
+
+def test_philox_words_match_aten_random_counters():
+    rng = np.random.default_rng(7)
+    ctrs = rng.integers(0, 2 ** 32, size=(64, 4), dtype=np.uint64)
+    seed = int(rng.integers(0, 2 ** 63))
+    mine = philox.philox4x32_10(ctrs, philox.seed_key(seed))
+    for i in range(ctrs.shape[0]):
+        assert np.array_equal(mine[i], aten_words(seed, ctrs[i]))
+
+
+def test_uniform_extremes():
+    lo = np.zeros((1, 4), dtype=np.uint32)
+    hi = np.full((1, 4), 0xFFFFFFFF, dtype=np.uint32)
+    u1, u2 = philox.uniforms(lo)
+    assert u1[0] == 2.0 ** -53 and u2[0] == 0.0
+    u1, u2 = philox.uniforms(hi)
+    assert u1[0] == 1.0 and u2[0] == 1.0 - 2.0 ** -53
+
+
+def test_box_muller_distribution():
+    from scipy import stats
+    x = philox.normal_pairs(seed=11, step=3, matrix_id=0, stream=0, npairs=100_000)
+    n = x.size
+    assert abs(x.mean()) < 5.0 / math.sqrt(n)
+    assert abs(x.var() - 1.0) < 5.0 * math.sqrt(2.0 / n)
+    assert stats.kstest(x, "norm").pvalue > 1e-3
+    # the two normals of one counter are uncorrelated
+    assert abs(np.corrcoef(x[0::2], x[1::2])[0, 1]) < 5.0 / math.sqrt(n / 2)
+    # fourth moment of N(0,1) is 3
+    assert abs((x ** 4).mean() - 3.0) < 0.1
+
+
+def test_sketch_layout_column_major_pairs():
+    rows, cols = 7, 5          # odd element count: last pair yields one normal
+    G = philox.sketch(3, 2, rows, cols, matrix_id=4)
+    flat = philox.normal_pairs(3, 2, 4, 0, (rows * cols + 1) // 2)
+    for c in range(cols):
+        for r in range(rows):
+            assert G[r, c] == flat[r + c * rows]
+    # different step / matrix id / stream give different draws
+    assert not np.allclose(G, philox.sketch(3, 3, rows, cols, matrix_id=4))
+    assert not np.allclose(G, philox.sketch(3, 2, rows, cols, matrix_id=5))
+
+
+# ------------------------------------------------------------ Householder ----
+
+def _explicit_H(v, tau):
+    r = v.numel()
+    return torch.eye(r, dtype=f64) - tau * torch.outer(v, v)
+
+
+def test_reflector_maps_to_e1():
+    g = torch.Generator().manual_seed(1)
+    for r in [1, 2, 5, 33]:
+        x = torch.randn(r, generator=g, dtype=f64)
+        v, tau, beta = oracle.householder_reflector(x)
+        H = _explicit_H(v, tau)
+        y = H @ x
+        e = torch.zeros(r, dtype=f64)
+        e[0] = float(beta)
+        assert torch.allclose(y, e, atol=1e-14 * float(x.norm()))
+        assert torch.allclose(H @ H.T, torch.eye(r, dtype=f64), atol=1e-15 * 8)
+        assert abs(abs(float(beta)) - float(x.norm())) < 1e-14 * float(x.norm())
+        if r > 1:
+            assert 1.0 <= float(tau) <= 2.0
+            assert float(beta) * float(x[0]) <= 0.0   # beta has the sign opposite to alpha
+
+
+def test_reflector_special_cases():
+    # x2 == 0: tau = 0 and H = I, even for negative alpha
+    v, tau, beta = oracle.householder_reflector(torch.tensor([-3.0, 0.0, 0.0], dtype=f64))
+    assert float(tau) == 0.0 and float(beta) == -3.0
+    v, tau, beta = oracle.householder_reflector(torch.tensor([2.5], dtype=f64))
+    assert float(tau) == 0.0 and float(beta) == 2.5
+    # alpha == 0: sgn(0) = +1, beta = -||x||
+    v, tau, beta = oracle.householder_reflector(torch.tensor([0.0, 3.0, 4.0], dtype=f64))
+    assert float(beta) == -5.0 and float(tau) == 1.0
+
+
+@pytest.mark.parametrize("r,c", [(50, 8), (9, 9), (64, 1), (13, 4)])
+def test_householder_qr_against_explicit_reflectors(r, c):
+    g = torch.Generator().manual_seed(r * 100 + c)
+    Y = torch.randn(r, c, generator=g, dtype=f64)
+    W, tau, R = oracle.householder_qr(Y)
+    Q = torch.eye(r, dtype=f64)
+    for j in range(c):
+        assert float(W[j, j]) == 1.0 and float(W[:j, j].abs().max() if j else 0.0) == 0.0
+        Q = Q @ _explicit_H(W[:, j], tau[j])
+    assert torch.allclose(Q[:, :c] @ R, Y, atol=1e-14 * float(Y.norm()))
+    assert torch.allclose(Q.T @ Q, torch.eye(r, dtype=f64), atol=1e-14)
+    assert torch.equal(R, torch.triu(R))
+    # third-party QR: |R_jj| is unique
+    Rn = np.linalg.qr(Y.numpy(), mode="r")
+    assert np.allclose(np.abs(np.diag(Rn)), np.abs(torch.diagonal(R).numpy()), rtol=1e-13)
+
+
+def test_wy_factor_equals_product_of_reflectors():
+    g = torch.Generator().manual_seed(5)
+    for (r, c) in [(40, 6), (6, 6), (17, 1), (30, 12)]:
+        Y = torch.randn(r, c, generator=g, dtype=f64)
+        W, tau, _ = oracle.householder_qr(Y)
+        S = oracle.wy_factor(W, tau)
+        Q = torch.eye(r, dtype=f64)
+        for j in range(c):
+            Q = Q @ _explicit_H(W[:, j], tau[j])
+        assert torch.equal(S, torch.triu(S))
+        assert torch.allclose(torch.eye(r, dtype=f64) - W @ S @ W.T, Q, atol=1e-14)
+
+
+def test_wy_factor_with_zero_tau():
+    # a column already in R form gives tau = 0 and must drop out of S
+    Y = torch.tensor([[1.0, 2.0], [0.0, 3.0], [0.0, 4.0]], dtype=f64)
+    W, tau, _ = oracle.householder_qr(Y)
+    assert float(tau[0]) == 0.0
+    S = oracle.wy_factor(W, tau)
+    Q = _explicit_H(W[:, 0], tau[0]) @ _explicit_H(W[:, 1], tau[1])
+    assert torch.allclose(torch.eye(3, dtype=f64) - W @ S @ W.T, Q, atol=1e-15)
+
+
+# ------------------------------------------------------------- small SVD ----
+
+def _check_svd(B, Us, D, Vs, tol=1e-14):
+    b = B.shape[0]
+    assert torch.allclose(Us @ torch.diag(D) @ Vs.T, B, atol=tol * max(1.0, float(B.norm())))
+    assert torch.allclose(Us.T @ Us, torch.eye(b, dtype=f64), atol=tol * 10)
+    assert torch.allclose(Vs.T @ Vs, torch.eye(b, dtype=f64), atol=tol * 10)
+    assert bool((D[:-1] >= D[1:]).all()) and bool((D >= 0).all())
+    for j in range(b):                      # sign rule
+        col = Vs[:, j]
+        idx = int(torch.nonzero(col.abs() == col.abs().max())[0, 0])
+        assert float(col[idx]) > 0
+
+
+def test_small_svd_diagonal_closed_form():
+    B = torch.diag(torch.tensor([3.0, -1.0, 2.0, 0.5], dtype=f64))
+    Us, D, Vs = oracle.small_svd(B)
+    assert torch.allclose(D, torch.tensor([3.0, 2.0, 1.0, 0.5], dtype=f64), rtol=0, atol=1e-15)
+    _check_svd(B, Us, D, Vs)
+    # V is a signed permutation with positive entries; U carries the sign of -1
+    assert torch.allclose(Vs.abs().sum(0), torch.ones(4, dtype=f64))
+    assert float(Vs.min()) >= 0
+    assert float(Us[1, 2]) == -1.0
+
+
+def test_small_svd_rank_one_closed_form():
+    x = torch.tensor([1.0, -2.0, 2.0], dtype=f64)
+    y = torch.tensor([0.0, 3.0, -4.0], dtype=f64)
+    B = torch.outer(x, y)
+    Us, D, Vs = oracle.small_svd(B)
+    assert abs(float(D[0]) - 15.0) < 1e-13
+    assert float(D[1:].abs().max()) < 1e-13
+    # largest entry of y/|y| is -4/5 -> the sign rule makes V[:,0] = -y/|y|
+    assert torch.allclose(Vs[:, 0], -y / 5.0, atol=1e-15)
+    assert torch.allclose(Us[:, 0], -x / 3.0, atol=1e-15)
+
+
+def test_small_svd_2x2_closed_form():
+    a, b_, d = 4.0, 3.0, -2.0
+    B = torch.tensor([[a, b_], [0.0, d]], dtype=f64)
+    Ssum = a * a + b_ * b_ + d * d
+    det = abs(a * d)
+    s1 = math.sqrt((Ssum + math.sqrt(Ssum * Ssum - 4 * det * det)) / 2)
+    s2 = det / s1
+    Us, D, Vs = oracle.small_svd(B)
+    assert abs(float(D[0]) - s1) < 1e-14 * s1 and abs(float(D[1]) - s2) < 1e-14 * s1
+    _check_svd(B, Us, D, Vs)
+
+
+def test_small_svd_random_and_orthogonal():
+    g = torch.Generator().manual_seed(9)
+    B = torch.randn(24, 24, generator=g, dtype=f64)
+    _check_svd(B, *oracle.small_svd(B))
+    Q, _ = torch.linalg.qr(torch.randn(10, 10, generator=g, dtype=f64))
+    Us, D, Vs = oracle.small_svd(Q)
+    assert torch.allclose(D, torch.ones(10, dtype=f64), atol=1e-14)
+
+
+# ------------------------------------------------------- whole randUTV ----
+
+SHAPES = [(64, 64, 16, 1), (80, 48, 16, 2), (48, 80, 16, 0), (70, 70, 24, 1), (33, 21, 7, 1),
+          (21, 33, 5, 2), (40, 40, 1, 1), (30, 30, 64, 1)]
+
+
+@pytest.mark.parametrize("m,n,b,q", SHAPES)
+def test_randutv_invariants(m, n, b, q):
+    A = inputs.gaussian(m, n, seed=m * 7 + n)
+    f = oracle.randutv(A, b, q, seed=1)
+    assert oracle.recon_error(A, f.U, f.T, f.V) < 1e-13
+    assert oracle.orth_error(f.U) < 1e-13 and oracle.orth_error(f.V) < 1e-13
+    # exact zeros: strictly lower part, and off-diagonal inside every diagonal block
+    assert float(torch.tril(f.T, -1).abs().max()) == 0.0
+    for (i, k, bi, rm, rn, right, left) in oracle.block_schedule(m, n, b):
+        blk = f.T[k:k + bi, k:k + bi]
+        assert torch.equal(blk, torch.diag(torch.diagonal(blk)))
+        assert bool((torch.diagonal(blk) >= 0).all())
+    # orthogonal invariance of the Frobenius norm
+    assert abs(float(f.T.norm() - A.norm())) < 1e-13 * float(A.norm())
+    # interlacing and tail bounds at every block boundary
+    sA = torch.linalg.svdvals(A)
+    for (i, k, bi, rm, rn, right, left) in oracle.block_schedule(m, n, b):
+        if k == 0:
+            continue
+        sT = torch.linalg.svdvals(f.T[:k, :k])
+        assert bool((sT <= sA[:k] * (1 + 1e-12) + 1e-13).all())
+        tail = f.T[k:, k:]
+        assert float(torch.linalg.matrix_norm(tail, 2)) >= float(sA[k]) * (1 - 1e-12)
+        assert float(tail.norm()) >= float(sA[k:].norm()) * (1 - 1e-12)
+
+
+def test_randutv_single_block_is_svd():
+    """b >= min(m,n): one step and T = diag(sigma(A)), the prescribed spectrum."""
+    for (m, n) in [(40, 40), (50, 30), (30, 50)]:
+        p = min(m, n)
+        sig = torch.exp(-torch.arange(p, dtype=f64) / 7.0)
+        A = inputs.prescribed(m, n, sig, seed=3)
+        f = oracle.randutv(A, 64, 1, seed=0)
+        d = torch.diagonal(f.T)
+        assert torch.allclose(d, sig, rtol=1e-12, atol=1e-14)
+        off = f.T.clone()
+        off[range(p), range(p)] = 0
+        assert float(off.abs().max()) < 1e-12
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_randutv_low_rank_first_block_captures_all(q):
+    """rank r <= b: after step 0 the trailing block is zero and D_0 = sigma."""
+    m, n, b, r = 72, 60, 12, 9
+    sig = torch.zeros(min(m, n), dtype=f64)
+    sig[:r] = torch.tensor([5.0, 4, 3, 2.5, 2, 1.5, 1, 0.7, 0.4], dtype=f64)
+    A = inputs.prescribed(m, n, sig, seed=4)
+    f = oracle.randutv(A, b, q, seed=2, max_steps=1)
+    assert float(f.T[b:, b:].norm()) < 1e-14 * float(A.norm()) * 10
+    assert torch.allclose(torch.diagonal(f.T)[:r], sig[:r], rtol=1e-12)
+
+
+def _literal_section_31(A, b, q, seed):
+    """§3.1 as written: dense U^(i), V^(i) per step and T^(i) = U^(i)^T T^(i-1) V^(i)."""
+    m, n = A.shape
+    T = A.clone()
+    U = torch.eye(m, dtype=f64)
+    V = torch.eye(n, dtype=f64)
+    for (i, k, bi, rm, rn, right, left) in oracle.block_schedule(m, n, b):
+        Vhat = torch.eye(rn, dtype=f64)
+        if right:
+            G = oracle.sketch(seed, i, rm, bi)
+            Y = oracle.range_basis(T[k:, k:], G, q)
+            W, tau, _ = oracle.householder_qr(Y)
+            for j in range(bi):
+                Vhat = Vhat @ _explicit_H(W[:, j], tau[j])
+        Uhat = torch.eye(rm, dtype=f64)
+        B = T[k:, k:] @ Vhat
+        if left:
+            W, tau, _ = oracle.householder_qr(B[:, :bi])
+            for j in range(bi):
+                Uhat = Uhat @ _explicit_H(W[:, j], tau[j])
+        C = (Uhat.T @ B)[:bi, :bi]
+        Us, D, Vs = oracle.small_svd(C)
+        Vi = torch.eye(n, dtype=f64)
+        Vi[k:, k:] = Vhat
+        Vsv = torch.eye(n, dtype=f64)
+        Vsv[k:k + bi, k:k + bi] = Vs
+        Vi = Vi @ Vsv
+        Ui = torch.eye(m, dtype=f64)
+        Ui[k:, k:] = Uhat
+        Usv = torch.eye(m, dtype=f64)
+        Usv[k:k + bi, k:k + bi] = Us
+        Ui = Ui @ Usv
+        T = Ui.T @ T @ Vi
+        U = U @ Ui
+        V = V @ Vi
+    return U, T, V
+
+
+@pytest.mark.parametrize("m,n,b,q", [(12, 12, 3, 1), (16, 10, 4, 0), (10, 16, 4, 2), (9, 7, 2, 1),
+                                     (8, 8, 1, 1), (11, 13, 4, 1)])
+def test_randutv_matches_literal_dense_products(m, n, b, q):
+    A = inputs.gaussian(m, n, seed=100 + m + n)
+    f = oracle.randutv(A, b, q, seed=6)
+    U, T, V = _literal_section_31(A, b, q, seed=6)
+    # same up to rounding; separated singular values make U and V unique
+    assert torch.allclose(f.T.triu(), T.triu(), atol=1e-13 * float(A.norm()))
+    assert torch.allclose(f.U, U, atol=1e-12)
+    assert torch.allclose(f.V, V, atol=1e-12)
+
+
+def test_resume_is_bitwise():
+    A = inputs.gaussian(50, 46, seed=8)
+    full = oracle.randutv(A, 8, 1, seed=5)
+    part = oracle.randutv(A, 8, 1, seed=5, max_steps=3)
+    rest = oracle.randutv(A, 8, 1, seed=5, state=part)
+    assert torch.equal(full.T, rest.T) and torch.equal(full.U, rest.U) and torch.equal(full.V, rest.V)
+
+
+def test_t_only_matches_with_factors():
+    A = inputs.gaussian(40, 36, seed=12)
+    a = oracle.randutv(A, 8, 1, seed=5)
+    b = oracle.randutv(A, 8, 1, seed=5, want_u=False, want_v=False)
+    assert torch.equal(a.T, b.T) and b.U is None and b.V is None
+
+
+def test_step_spectrum_is_revealed():
+    """q >= 1 on a gapped spectrum: |T_kk| tracks sigma_k away from the gap's block."""
+    n, b, gap = 192, 16, 40
+    sig = inputs.spectrum("step", n, gap)
+    A = inputs.prescribed(n, n, sig, seed=2)
+    f = oracle.randutv(A, b, 1, seed=0)
+    d = torch.diagonal(f.T)
+    straddle = range((gap // b) * b, (gap // b + 1) * b)
+    for k in range(n):
+        if k in straddle:
+            continue
+        assert abs(float(d[k]) / float(sig[k]) - 1.0) < 1e-3, k
+
+
+def test_fig3_schedule_golden():
+    rows = []
+    with open(os.path.join(GOLDEN, "fig3_task_order.txt")) as fh:
+        for line in fh:
+            line = line.strip()
+            if line and not line.startswith("#"):
+                rows.append(tuple(int(t) for t in line.split()))
+    n = 64
+    sched = oracle.block_schedule(n, n, n // 2)
+    got = [(i, int(right), int(left), 1) for (i, k, bi, rm, rn, right, left) in sched]
+    assert got == rows
+
+
+# ------------------------------------------------------------ low rank ----
+
+def test_lowrank_is_paper_definition():
+    m, n, b, k = 60, 50, 8, 16
+    A = inputs.gaussian(m, n, seed=21)
+    full = oracle.randutv(A, b, 1, seed=3)
+    Ak_def = full.U[:, :k] @ full.T[:k, :] @ full.V.T          # §1.1 definition
+    assert torch.allclose(oracle.lowrank(A, k, b, 1, seed=3), Ak_def, atol=1e-13)
+
+
+def test_lowrank_of_rank_k_matrix_is_itself():
+    m, n, b, k = 40, 36, 8, 16
+    sig = torch.zeros(36, dtype=f64)
+    sig[:k] = torch.linspace(3, 1, k, dtype=f64)
+    A = inputs.prescribed(m, n, sig, seed=5)
+    assert torch.allclose(oracle.lowrank(A, k, b, 1, seed=1), A, atol=1e-13)
+
+
+# ------------------------------------------------------------- flops ----
+
+def test_flop_count_leading_order():
+    for q in [0, 1, 2]:
+        n = 16384
+        f = inputs.algorithmic_flops(n, n, 128, q)
+        assert abs(f / ((8 + 4 * q / 3) * n ** 3) - 1) < 0.03
+        f = inputs.algorithmic_flops(n, n, 128, q, want_u=False, want_v=False)
+        assert abs(f / ((4 + 4 * q / 3) * n ** 3) - 1) < 0.03
+
+
+# ----------------------------------------------- sketch and power iteration ----
+
+def _known_svd(m, n, seed):
+    p = min(m, n)
+    sig = torch.exp(-torch.arange(p, dtype=f64) / 6.0)
+    Q1 = inputs.haar_orthogonal(m, seed, inputs.STREAM_Q1, p)
+    Q2 = inputs.haar_orthogonal(n, seed, inputs.STREAM_Q2, p)
+    return Q1, sig, Q2, (Q1 * sig) @ Q2.T
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_range_basis_closed_form(q):
+    """Y = (A^T A)^q A^T G = Q2 diag(sigma^(2q+1)) Q1^T G for A = Q1 diag(sigma) Q2^T."""
+    Q1, sig, Q2, A = _known_svd(30, 24, seed=7)
+    G = oracle.sketch(4, 0, 30, 5)
+    Y = oracle.range_basis(A, G, q)
+    Yref = (Q2 * sig ** (2 * q + 1)) @ (Q1.T @ G)
+    assert torch.allclose(Y, Yref, atol=1e-14 * float(Yref.abs().max()) * 10)
+
+
+@pytest.mark.parametrize("q", [0, 1, 2])
+def test_first_block_of_v_spans_the_sketched_range(q):
+    """After step 0, V(:, 0:b) spans Y_0 = Q2 diag(sigma^(2q+1)) Q1^T G_0 (§3.1)."""
+    m, n, b = 40, 32, 6
+    Q1, sig, Q2, A = _known_svd(m, n, seed=9)
+    f = oracle.randutv(A, b, q, seed=13, max_steps=1)
+    G0 = oracle.sketch(13, 0, m, b)
+    Yref = (Q2 * sig ** (2 * q + 1)) @ (Q1.T @ G0)
+    Vb = f.V[:, :b]
+    resid = Yref - Vb @ (Vb.T @ Yref)
+    assert float(resid.norm()) < 1e-12 * float(Yref.norm())
+    # and the sketch of the other q values is not in that span
+    for q2 in {0, 1, 2} - {q}:
+        Y2 = (Q2 * sig ** (2 * q2 + 1)) @ (Q1.T @ G0)
+        assert float((Y2 - Vb @ (Vb.T @ Y2)).norm()) > 1e-6 * float(Y2.norm())
