@@ -1,0 +1,350 @@
+"""Benchmark: randUTV TFLOP/s on GB300 (one JSON line on stdout, rank 0).
+
+One step = one full factorization A = U T V^T (every block step of the
+method: sketch, power iteration, the two Householder QRs with their
+compact-WY updates of T, U and V, and the small SVD with its fold-back) of
+the 16384 x 16384 FP64 workload, b = 128, q = 1, on a seeded i.i.d. N(0,1)
+input.  TFLOP/s counts algorithmic flops (leading terms summed per step).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+--impl reference times the CPU oracle (FP64, the host's cores) on a bounded
+sample of the same workload: the first block step(s) of the same 16384^2
+factorization.  Under torchrun every rank factors its own matrix (replicas:
+the factorization has no data-parallel split without an exchange per step),
+and the value is the flops of all ranks over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2002_06960_gb300 import inputs  # noqa: E402
+
+METRIC = "randUTV TFLOP/s & % of peak at n=16384, FP64 vs mixed precision at stated error"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--b", type=int, default=128)
+    ap.add_argument("--q", type=int, default=1)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-steps", type=int, default=1,
+                    help="block steps of the oracle in the CPU-baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ ranks
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64,
+                     device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------- clocks
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ peaks
+
+def fp64_peak(sm_max_mhz=None):
+    """FP64 DFMA roofline: SMs x 2 DFMA/clk (4 flops) x max SM clock."""
+    peaks = {}
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        peaks = json.load(open(p))
+    mhz = peaks.get("sm_max_mhz") or sm_max_mhz or 2070.0
+    sms = torch.cuda.get_device_properties(0).multi_processor_count if torch.cuda.is_available() else 152
+    return sms * 4.0 * mhz * 1e6 / 1e12, mhz, sms
+
+
+# ------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local):
+    import paper_2002_06960_gb300 as pkg
+
+    n, b, q = args.n, args.b, args.q
+    seed = args.seed + rank
+    flops = inputs.algorithmic_flops(n, n, b, q)
+    # input: seeded N(0,1) on the host (pinned), copied once for the device-resident timing
+    A_host = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    A_host.copy_(inputs.gaussian(n, n, seed))
+    A = pkg.colmajor_empty(n, n, device="cuda")
+    A.copy_(A_host, non_blocking=False)
+    U = pkg.colmajor_empty(n, n)
+    T = pkg.colmajor_empty(n, n)
+    V = pkg.colmajor_empty(n, n)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def step():
+        with torch.cuda.stream(stream):
+            pkg.randutv_factor_ex(A, b, q, 0, U=U, T=T, V=V)
+
+    for _ in range(args.warmup):
+        step()
+    with torch.cuda.stream(stream):
+        st = pkg.randutv_stream_status()
+    if st != 0:
+        raise RuntimeError(f"warm-up step failed with status {st}")
+
+    clocks = ClockSampler(local)
+    pkg.randutv_launch_count(reset=True)
+    pkg.randutv_profile_enable(True)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = pkg.randutv_launch_count()
+    prof = pkg.randutv_profile_read()
+    pkg.randutv_profile_enable(False)
+    with torch.cuda.stream(stream):
+        st = pkg.randutv_stream_status()
+    if st != 0:
+        raise RuntimeError(f"timed step failed with status {st}")
+    ms_max = max_over_ranks(ms, world)
+
+    # errors of the result (sampled rows / columns: exact products would cost a step)
+    g = torch.Generator().manual_seed(0)
+    rows = torch.randperm(n, generator=g)[:64].cuda()
+    rec = (U[rows, :] @ T) @ V.T
+    recon = float(torch.linalg.norm(rec - A[rows, :]) / torch.linalg.norm(A[rows, :]))
+    cols = torch.randperm(n, generator=g)[:64].cuda()
+    eye = torch.zeros(n, 64, dtype=torch.float64, device="cuda")
+    eye[cols, torch.arange(64, device="cuda")] = 1.0
+    orth_u = float(torch.linalg.norm(U.T @ U[:, cols] - eye) / 8.0)
+    orth_v = float(torch.linalg.norm(V.T @ V[:, cols] - eye) / 8.0)
+
+    # end to end through the public C-ABI with host buffers (copies inside)
+    Uh = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    Th = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    Vh = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        pkg.randutv_factor_host(A_host, b, q, 0, Uh, Th, Vh)
+        float(Th[0, 0])  # the read-back
+    e2e_s = (time.perf_counter() - t0) / args.e2e_steps
+    e2e_s = max_over_ranks(e2e_s, world)
+
+    peak, mhz, sms = fp64_peak()
+    g_ = prof.get("dgemm", {"ms": 0.0, "flops": 0.0, "launches": 0})
+    dgemm_tf = g_["flops"] / (g_["ms"] * 1e-3) / 1e12 if g_["ms"] > 0 else 0.0
+    total_prof_ms = sum(v["ms"] for v in prof.values())
+    shares = {k: round(v["ms"] / total_prof_ms, 4) for k, v in prof.items() if total_prof_ms > 0}
+    per_launch = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                      "avg_us": round(1000 * v["ms"] / v["launches"], 2) if v["launches"] else 0}
+                  for k, v in prof.items()}
+    value = world * flops / (ms_max * 1e-3) / 1e12
+    out = {
+        "metric": METRIC,
+        "value": round(value, 4),
+        "unit": "TFLOP/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_max, 2),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"randutv_fp64_n{n}_b{b}_q{q}", "m": n, "n": n, "b": b, "q": q,
+                   "input": "i.i.d. N(0,1), seeded", "outputs": "U, T, V",
+                   "precision": "FP64 throughout",
+                   "l2": "inputs larger than L2 (A 2 GiB, U/T/V 6 GiB per step)",
+                   "parallelism": f"replicas x{world}", "algorithmic_flops_per_step": flops,
+                   "t_over_n3_1e10": round(ms_max * 1e-3 / n ** 3 * 1e10, 5)},
+        "roofline": {"bound": "alu", "kernel": "dgemm (FP64 DFMA)",
+                     "achieved": round(dgemm_tf, 4), "peak": round(peak, 4), "unit": "TFLOP/s",
+                     "frac": round(dgemm_tf / peak, 4),
+                     "peak_source": f"{sms} SMs x 2 DFMA/clk x 2 flops x {mhz:.0f} MHz "
+                                    "(DFMA unit count x max SM clock)",
+                     "traffic": None,
+                     "whole_step_frac": round(value / world / peak, 4)},
+        "kernel_shares": shares,
+        "kernels": per_launch,
+        "errors": {"recon_sampled_rows": recon, "orth_u_sampled": orth_u,
+                   "orth_v_sampled": orth_v},
+        "e2e": {"value": round(world * flops / e2e_s / 1e12, 4), "unit": "TFLOP/s",
+                "h2d_bytes_per_step": n * n * 8, "d2h_bytes_per_step": 3 * n * n * 8,
+                "seconds_per_step": round(e2e_s, 3)},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    return out, A_host
+
+
+# ---------------------------------------------------------- oracle (CPU)
+
+def oracle_sample(n, b, q, seed, steps, A=None):
+    """Times the CPU oracle on the first `steps` block steps of the workload."""
+    import oracle
+    if A is None:
+        A = inputs.gaussian(n, n, seed)
+    A = A.contiguous() if not A.is_contiguous() else A
+    flops = _flops_first_steps(n, b, q, steps)
+    t0 = time.perf_counter()
+    oracle.randutv(A, b, q, 0, max_steps=steps)
+    dt = time.perf_counter() - t0
+    return {"value": round(flops / dt / 1e12, 6), "unit": "TFLOP/s",
+            "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"first {steps} block step(s) of the {n}x{n} b={b} q={q} FP64 "
+                      f"factorization with U and V ({flops:.3e} algorithmic flops, {dt:.1f} s)"}
+
+
+def _flops_first_steps(n, b, q, steps):
+    return inputs.algorithmic_flops(n, n, b, q, max_steps=steps)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return None
+    n, b, q = args.n, args.b, args.q
+    A = inputs.gaussian(n, n, args.seed)
+    for _ in range(args.warmup):
+        oracle_sample(n, b, q, args.seed, 1, A)
+    vals = [oracle_sample(n, b, q, args.seed, 1, A) for _ in range(args.steps)]
+    v = statistics.median(x["value"] for x in vals)
+    flops = _flops_first_steps(n, b, q, 1)
+    sec = flops / (v * 1e12)
+    cb = dict(vals[0])
+    cb["value"] = v
+    return {
+        "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 1), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": f"randutv_fp64_n{n}_b{b}_q{q}", "m": n, "n": n, "b": b, "q": q,
+                   "input": "i.i.d. N(0,1), seeded",
+                   "sample": "each step is the first block step of the factorization"},
+        "cpu_baseline": cb,
+        "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        out = run_reference(args, world, rank)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, A_host = run_ours(args, world, rank, local)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = oracle_sample(args.n, args.b, args.q, args.seed,
+                                                args.cpu_steps, A_host.contiguous())
+        except Exception as e:  # report, never hide
+            out["cpu_baseline"] = {"value": None, "error": repr(e)}
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

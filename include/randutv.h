@@ -1,0 +1,178 @@
+/*
+ * randutv.h -- C-ABI of the GB300 randUTV library.
+ *
+ * randUTV (Heavner, Martinsson & Quintana-Orti, "Computing rank-revealing
+ * factorizations of matrices stored out-of-core", arXiv 2002.06960, §3.1 and
+ * Fig. 2) factors an m x n matrix as A = U T V^T with U (m x m) and V (n x n)
+ * orthogonal and T (m x n) upper triangular, one block of b columns per step:
+ * a Gaussian sketch and power iteration give the block of V, a Householder QR
+ * of the new column panel gives the block of U, and a b x b SVD makes the
+ * diagonal block of T diagonal.
+ *
+ * Conventions for every entry point below:
+ *  - Matrices are column-major with a leading dimension (ld >= rows).
+ *  - Pointers are DEVICE pointers (memory of the current CUDA device) unless
+ *    the name ends in _host.  The caller owns every buffer it passes; the
+ *    library never frees caller memory.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Entry points ending in _ex are asynchronous on that stream;
+ *    the others synchronize before returning.
+ *  - Return value: 0 on success; -i if argument i (1-based) is invalid
+ *    (LAPACK style); a positive randutv_status otherwise.  No C++ exception
+ *    crosses this boundary.
+ *  - Scratch memory is allocated by the library on first use per device and
+ *    kept until randutv_finalize(); it grows when a larger problem needs it.
+ *  - Device-side waits are bounded (about two seconds); a wait that runs out
+ *    makes the call return RANDUTV_ETIMEOUT and leaves the outputs undefined.
+ */
+#ifndef RANDUTV_H
+#define RANDUTV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RANDUTV_OK = 0,
+  RANDUTV_ECUDA = 1,      /* a CUDA runtime call failed (message: randutv_last_error) */
+  RANDUTV_ENONFINITE = 2, /* the input holds NaN or Inf */
+  RANDUTV_ETIMEOUT = 3,   /* a bounded device-side wait ran out */
+  RANDUTV_ENOMEM = 4,     /* scratch allocation failed */
+  RANDUTV_EUNSUPPORTED = 5 /* valid arguments outside what this build supports */
+} randutv_status;
+
+typedef enum {
+  RANDUTV_FP64 = 0 /* every step in FP64 */
+} randutv_prec;
+
+/* ---------------------------------------------------------------- factor --
+ * Full blocked randUTV, §3.1 steps 1-6 with the update list of Fig. 2.
+ *   m, n    (args 1, 2)  sizes, m >= 1, n >= 1.
+ *   A       (3)  m x n input, read only, leading dimension lda >= m (4).
+ *   b       (5)  block size, 1 <= b <= 256.
+ *   q       (6)  power-iteration count, 0 <= q <= 16.
+ *   seed    (7)  key of the Philox sketch generator (see randutv_philox_normal).
+ *   U       (8)  m x m output, ld m, or NULL to skip U.
+ *   T       (9)  m x n output, ld m; may alias A only when lda == m.
+ *   V       (10) n x n output, ld n, or NULL to skip V.
+ * On return T is upper triangular with exact zeros below the diagonal, every
+ * b x b diagonal block is diagonal with non-negative entries in descending
+ * order, and A = U T V^T up to rounding.  Returns RANDUTV_ENONFINITE when A
+ * holds NaN or Inf (checked before any work).
+ */
+int randutv_factor(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
+                   uint64_t seed, double* U, double* T, double* V);
+
+/* As randutv_factor, asynchronous on `stream` (arg 12), with two extras:
+ *   max_steps (11)  stop after this many block steps (a partial factorization
+ *                   whose first max_steps*b columns of U, V are final); a
+ *                   negative value runs to completion.
+ *   first_step(13)  resume: treat U, T, V as the state after `first_step`
+ *                   steps of an earlier call with the same arguments, and
+ *                   continue from there (0 = start from A; A is then unread).
+ * Because the sketch of step i depends only on (seed, i), a resumed run gives
+ * bitwise the same result as an uninterrupted one.  Errors detected on the
+ * device are reported by randutv_stream_status() after the stream completes.
+ */
+int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
+                      uint64_t seed, double* U, double* T, double* V, int max_steps,
+                      void* stream, int first_step);
+
+/* randutv_factor with HOST buffers (pageable or pinned): A is copied to the
+ * device, factored, and U, T, V copied back; same arguments and layout. */
+int randutv_factor_host(int64_t m, int64_t n, const double* A_host, int64_t lda, int b, int q,
+                        uint64_t seed, double* U_host, double* T_host, double* V_host);
+
+/* Status word of the last _ex call on `stream` (synchronizes the stream). */
+int randutv_stream_status(void* stream);
+
+/* ------------------------------------------------------------ components --
+ * The steps of one block, exposed so that each can be checked on its own.
+ */
+
+/* Gaussian sketch of one step (§3.1, construction of V-hat, step 1): G is
+ * rows x cols, column-major with ld = rows.  Element l = r + c*rows takes
+ * pair p = l >> 1 of Philox4x32-10 with key (lo32(seed), hi32(seed)) and
+ * counter (p, step, matrix_id, stream_id); the pair's 53-bit uniforms
+ * u1 = (j1 + 1) 2^-53, u2 = j2 2^-53 (j = (x0 >> 5) 2^26 + (x1 >> 6) and
+ * likewise from x2, x3) give sqrt(-2 ln u1) cos(2 pi u2) for even l and
+ * sqrt(-2 ln u1) sin(2 pi u2) for odd l. */
+int randutv_philox_normal(uint64_t seed, uint32_t step, uint32_t matrix_id, uint32_t stream_id,
+                          int64_t rows, int64_t cols, double* G, void* stream);
+
+/* Raw Philox4x32-10 words for counters (c0 + i, c1, c2, c3), i = 0..count-1;
+ * out is 4*count uint32 (device). */
+int randutv_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                         int64_t count, uint32_t* out, void* stream);
+
+/* Unpivoted Householder QR of an r x c panel, r >= c, in place (Fig. 2,
+ * unpivoted_QR).  On return the upper triangle of the top c x c holds R and
+ * the part below the diagonal is exactly zero; W (r x c, ld r) is the unit
+ * lower trapezoidal matrix of reflector vectors and tau (c) their scalars,
+ * with H_j = I - tau_j w_j w_j^T and panel_in = H_1 ... H_c [R; 0].
+ * Reflector convention: for x = (alpha, x2), s = ||x2||; s == 0 gives
+ * tau = 0 (H = I); otherwise beta = -sgn(alpha) sqrt(alpha^2 + s^2),
+ * sgn(0) = +1, tau = (beta - alpha)/beta, w = (1, x2/(alpha - beta)). */
+int randutv_householder_qr(int64_t r, int64_t c, double* panel, int64_t ld, double* W,
+                           double* tau, void* stream);
+
+/* Compact-WY factor (Fig. 2: T_V, T_U): S (c x c, ld c, upper triangular)
+ * with H_1 ... H_c = I - W S W^T, for W (r x c, ld r) and tau from
+ * randutv_householder_qr. */
+int randutv_wy_factor(int64_t r, int64_t c, const double* W, const double* tau, double* S,
+                      void* stream);
+
+/* SVD of a b x b block (Fig. 2: [A11, U_SVD, V_SVD] := SVD(A11)), one-sided
+ * Jacobi in FP64: B = Us diag(D) Vs^T with D descending and >= 0; each column
+ * of Vs has its entry of largest magnitude (lowest row on ties) positive and
+ * the matching column of Us carries the same sign.  B (ld ldb) is read only;
+ * Us, Vs are b x b with ld b; 1 <= b <= 256. */
+int randutv_small_svd(int64_t b, const double* B, int64_t ldb, double* D, double* Us, double* Vs,
+                      void* stream);
+
+/* C = alpha op(A) op(B) + beta C in FP64 (the products of every step);
+ * transa/transb are 'N' or 'T'. */
+int randutv_dgemm(char transa, char transb, int64_t M, int64_t N, int64_t K, double alpha,
+                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
+                  double* C, int64_t ldc, void* stream);
+
+/* ------------------------------------------------------------- utilities -- */
+
+/* Bytes of library scratch one factorization of this shape needs. */
+size_t randutv_workspace_bytes(int64_t m, int64_t n, int b, int prec);
+
+/* Frees the library's scratch on every device it was allocated on. */
+void randutv_finalize(void);
+
+/* Short description of a status code. */
+const char* randutv_strerror(int status);
+
+/* Text of the last CUDA error seen by this thread ("" if none). */
+const char* randutv_last_error(void);
+
+/* Number of kernel launches issued by this process since the last reset. */
+uint64_t randutv_launch_count(int reset);
+
+/* Tracing.  While enabled (on != 0), every kernel launch of the library is
+ * bracketed by a pair of CUDA events on its stream and tagged with its kernel
+ * class and the algorithmic flops and bytes of that launch.  Enabling clears
+ * the records.  Timing adds two event records per launch. */
+void randutv_profile_enable(int on);
+
+/* Synchronizes on the recorded events and writes, per kernel class c
+ * (0 <= c < nclass), out[4c..4c+3] = {launches, milliseconds, flops, bytes},
+ * then clears the records.  Returns the number of classes the library
+ * defines (write at most nclass of them), or a status code < 0 / > 0. */
+int randutv_profile_read(double* out, int nclass);
+
+/* Name of kernel class `cls` ("dgemm", "jacobi_svd", ...). */
+const char* randutv_profile_class_name(int cls);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RANDUTV_H */

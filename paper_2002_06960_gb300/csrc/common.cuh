@@ -1,0 +1,138 @@
+// Shared device/host helpers of the randUTV library (sm_103a).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/randutv.h"
+
+namespace rutv {
+
+// ----------------------------------------------------------------- host side
+
+// Records a CUDA error for randutv_last_error() and returns RANDUTV_ECUDA.
+int cuda_fail(cudaError_t e, const char* what);
+
+#define RUTV_CK(call)                                     \
+  do {                                                    \
+    cudaError_t _e = (call);                              \
+    if (_e != cudaSuccess) return ::rutv::cuda_fail(_e, #call); \
+  } while (0)
+
+// Counts kernel launches (the library's own kernels only).
+void note_launch(int n = 1);
+
+// Per-kernel-class timing (tracing): when enabled, every launch of the
+// library is bracketed by a CUDA event pair on its stream and tagged with the
+// algorithmic flops and bytes of that launch.
+enum KernelClass { K_PHILOX = 0, K_DGEMM, K_QR, K_WY, K_SVD, K_OTHER, K_NCLASS };
+struct ProfScope {
+  ProfScope(int cls, double flops, double bytes, cudaStream_t st);
+  ~ProfScope();
+  int slot;
+  cudaStream_t st;
+};
+
+// Device properties cached per device.
+struct DevInfo {
+  int sms;
+  int smem_optin;
+};
+const DevInfo& dev_info();
+
+// Scratch: one growing allocation per device, carved into aligned pieces.
+struct Arena {
+  char* base = nullptr;
+  size_t cap = 0;
+  size_t used = 0;
+  void* take(size_t bytes) {
+    size_t off = (used + 255) & ~size_t(255);
+    used = off + bytes;
+    return base + off;
+  }
+};
+// Makes sure the device scratch holds at least `bytes`; returns status.
+int scratch_reserve(size_t bytes, Arena* out);
+
+// Words of device status shared by the kernels of one call: [0] error code,
+// [1] where the error happened, [2..3] barrier counter and generation.
+struct StatusWords {
+  unsigned* words;  // device, 64 words
+};
+
+// Milliseconds a bounded device-side wait may spin before it gives up.
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+// ---------------------------------------------------------------- device side
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier for a cooperatively launched grid (all CTAs resident).
+// `bar` points at two words {arrival count, generation} that start at
+// {0, any}.  Every wait is bounded: after kWaitLimitNs the waiting CTA sets
+// err[0] = RANDUTV_ETIMEOUT (err[1] = `site`) and every CTA then returns
+// false from this and every later barrier, so the kernel can leave early.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err,
+                                             unsigned site) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    if (ld_acquire_gpu(err) != 0) {
+      ok = 0;
+    } else {
+      unsigned gen = ld_acquire_gpu(bar + 1);
+      __threadfence();
+      unsigned arrived = atomicAdd(bar, 1u);
+      if (arrived == nblocks - 1) {
+        atomicExch(bar, 0u);
+        __threadfence();
+        st_release_gpu(bar + 1, gen + 1);
+      } else {
+        unsigned long long t0 = globaltimer_ns();
+        unsigned spins = 0;
+        while (ld_acquire_gpu(bar + 1) == gen) {
+          if (ld_acquire_gpu(err) != 0) { ok = 0; break; }
+          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
+            if (atomicCAS(err, 0u, (unsigned)RANDUTV_ETIMEOUT) == 0u) atomicExch(err + 1, site);
+            ok = 0;
+            break;
+          }
+          __nanosleep(32);
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Deterministic block-wide sum (fixed tree); `red` is blockDim.x/32 doubles.
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < nw; ++i) s += red[i];
+  return s;
+}
+
+}  // namespace rutv

@@ -1,0 +1,180 @@
+// Householder QR of a tall panel and its compact-WY factor (FP64).
+//
+// Fig. 2 takes an unpivoted QR twice per block step: of the sketch Y (its
+// reflectors W_V form V-hat, §3.1 V-hat step 2) and of the new column panel
+// [A11; A21] (reflectors W_U, §3.1 step 2), and applies each as
+// I - W S W^T (S is the triangular factor the paper calls T_V / T_U).
+//
+// The panel has r rows (up to the matrix height) and c <= 256 columns, so
+// the reflector of each column needs a reduction over all r rows.  One
+// cooperative grid (one CTA per SM at most) walks the columns: each CTA owns
+// a contiguous slice of rows, and two bounded grid barriers per column
+// separate (1) the partial squared norms below the diagonal, (2) the partial
+// dot products of the reflector with the trailing columns, and (3) the rank-1
+// update.  Every cross-CTA sum is taken in CTA order, so the result is
+// bitwise reproducible.  Values written by another CTA (the partial sums and
+// the diagonal entry) are read with L2-only loads: L1 is not coherent
+// across SMs.
+#include "common.cuh"
+
+namespace rutv {
+
+namespace {
+constexpr int QR_THREADS = 256;
+
+struct QrArgs {
+  int64_t r, c;
+  double* A;
+  int64_t lda;
+  double* W;       // r x c, ld r
+  double* tau;     // c
+  double* part1;   // nblocks
+  double* part2;   // nblocks x c
+  unsigned* bar;   // {count, generation}
+  unsigned* err;
+};
+
+__global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a) {
+  __shared__ double red[QR_THREADS / 32];
+  __shared__ double s_coef[4];  // tau, scale, beta, (unused)
+  const unsigned nb = gridDim.x;
+  const int64_t rows_per = (a.r + nb - 1) / nb;
+  const int64_t i0 = (int64_t)blockIdx.x * rows_per;
+  const int64_t i1 = (i0 + rows_per < a.r) ? i0 + rows_per : a.r;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = QR_THREADS / 32;
+
+  // W starts as zero above the diagonal; column j is written in step 3 of j.
+  for (int64_t j = 0; j < a.c; ++j) {
+    // ---- phase 1: partial sum of squares of A(j+1:r, j) over own rows
+    double ss = 0.0;
+    {
+      const int64_t lo = (i0 > j + 1) ? i0 : j + 1;
+      for (int64_t i = lo + threadIdx.x; i < i1; i += QR_THREADS) {
+        const double x = a.A[i + j * a.lda];
+        ss = fma(x, x, ss);
+      }
+    }
+    ss = block_sum(ss, red);
+    if (threadIdx.x == 0) a.part1[blockIdx.x] = ss;
+    if (!grid_barrier(a.bar, nb, a.err, 1)) return;
+
+    // ---- phase 2: reflector scalars (every CTA, same order), partial dots
+    if (threadIdx.x == 0) {
+      double sig2 = 0.0;
+      for (unsigned t = 0; t < nb; ++t) sig2 += __ldcg(a.part1 + t);
+      const double alpha = __ldcg(a.A + j + j * a.lda);  // row j may be another CTA's
+      double tau, scale, beta;
+      if (sig2 == 0.0) {
+        tau = 0.0; beta = alpha; scale = 0.0;
+      } else {
+        const double nrm = sqrt(fma(alpha, alpha, sig2));
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      s_coef[0] = tau; s_coef[1] = scale; s_coef[2] = beta;
+    }
+    __syncthreads();
+    const double tau = s_coef[0], scale = s_coef[1];
+    // dot_l = sum_{i >= j} v_i A(i, l) for l > j, v_j = 1, v_i = A(i,j) * scale
+    for (int64_t l = j + 1 + warp; l < a.c; l += nwarp) {
+      double d = 0.0;
+      const int64_t lo = (i0 > j) ? i0 : j;
+      for (int64_t i = lo + lane; i < i1; i += 32) {
+        const double v = (i == j) ? 1.0 : a.A[i + j * a.lda] * scale;
+        d = fma(v, a.A[i + l * a.lda], d);
+      }
+      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+      if (lane == 0) a.part2[(int64_t)blockIdx.x * a.c + l] = d;
+    }
+    if (!grid_barrier(a.bar, nb, a.err, 2)) return;
+
+    // ---- phase 3: rank-1 update of own rows, write W(:, j), R(j, j), zeros
+    // w_l = tau * sum_t part2[t][l]  (each warp sums the columns it updates)
+    for (int64_t l = j + 1 + warp; l < a.c; l += nwarp) {
+      double wl = 0.0;
+      if (lane == 0) {
+        for (unsigned t = 0; t < nb; ++t) wl += __ldcg(a.part2 + (int64_t)t * a.c + l);
+        wl *= tau;
+      }
+      wl = __shfl_sync(0xffffffffu, wl, 0);
+      if (tau != 0.0) {
+        const int64_t lo = (i0 > j) ? i0 : j;
+        for (int64_t i = lo + lane; i < i1; i += 32) {
+          const double v = (i == j) ? 1.0 : a.A[i + j * a.lda] * scale;
+          a.A[i + l * a.lda] = fma(-v, wl, a.A[i + l * a.lda]);
+        }
+      }
+    }
+    __syncthreads();  // the updates above read A(:, j); rewrite it only now
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += QR_THREADS) {
+      double wv;
+      if (i < j) wv = 0.0;
+      else if (i == j) wv = 1.0;
+      else wv = (tau != 0.0) ? a.A[i + j * a.lda] * scale : 0.0;
+      a.W[i + j * a.r] = wv;
+      if (i > j) a.A[i + j * a.lda] = 0.0;
+      if (i == j) a.A[i + j * a.lda] = s_coef[2];
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) a.tau[j] = tau;
+    __syncthreads();
+  }
+}
+
+// S (c x c, ld c) from the Gram matrix Gm = W^T W (c x c, ld c) and tau:
+// S_jj = tau_j, S(0:j, j) = -tau_j S(0:j, 0:j) Gm(0:j, j).  One CTA.
+__global__ void wy_factor_kernel(int64_t c, const double* __restrict__ Gm,
+                                 const double* __restrict__ tau, double* __restrict__ S) {
+  for (int64_t e = threadIdx.x; e < c * c; e += blockDim.x) S[e] = 0.0;
+  __syncthreads();
+  for (int64_t j = 0; j < c; ++j) {
+    const double tj = tau[j];
+    for (int64_t i = threadIdx.x; i < j; i += blockDim.x) {
+      double s = 0.0;
+      for (int64_t l = i; l < j; ++l) s = fma(S[i + l * c], Gm[l + j * c], s);
+      S[i + j * c] = -tj * s;
+    }
+    if (threadIdx.x == 0) S[j + j * c] = tj;
+    __syncthreads();
+  }
+}
+}  // namespace
+
+size_t householder_scratch_bytes(int64_t c) {
+  const int nb = dev_info().sms;
+  return (size_t)nb * sizeof(double) + (size_t)nb * (size_t)c * sizeof(double) + 512;
+}
+
+int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* W, double* tau,
+                          char* scratch, unsigned* bar, unsigned* err, cudaStream_t st) {
+  if (c <= 0) return 0;
+  const int sms = dev_info().sms;
+  int nb = (int)((r + 63) / 64);  // at least 64 rows per CTA
+  if (nb > sms) nb = sms;
+  if (nb < 1) nb = 1;
+  QrArgs a;
+  a.r = r; a.c = c; a.A = A; a.lda = lda; a.W = W; a.tau = tau;
+  a.part1 = (double*)scratch;
+  a.part2 = a.part1 + sms;
+  a.bar = bar; a.err = err;
+  ProfScope prof(K_QR, 2.0 * (double)c * c * ((double)r - c / 3.0), 24.0 * (double)r * c, st);
+  RUTV_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  void* args[] = {&a};
+  RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel, dim3(nb),
+                                      dim3(QR_THREADS), args, 0, st));
+  note_launch();
+  return 0;
+}
+
+int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st) {
+  if (c <= 0) return 0;
+  int threads = (int)((c + 31) / 32 * 32);
+  if (threads > 256) threads = 256;
+  ProfScope prof(K_WY, (double)c * c * c / 3.0, 16.0 * (double)c * c, st);
+  wy_factor_kernel<<<1, threads, 0, st>>>(c, Gm, tau, S);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace rutv

@@ -1,0 +1,27 @@
+// Launchers of the device kernels (one translation unit each).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+namespace rutv {
+
+int launch_philox_normal(uint64_t seed, uint32_t step, uint32_t mid, uint32_t sid, int64_t rows,
+                         int64_t cols, double* G, int64_t ldg, cudaStream_t st);
+int launch_philox_words(uint64_t seed, uint4 c, int64_t count, uint32_t* out, cudaStream_t st);
+
+size_t dgemm_scratch_bytes(int64_t M, int64_t N);
+int launch_dgemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
+                 int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
+                 double* scratch, size_t scratch_bytes, cudaStream_t st);
+
+size_t householder_scratch_bytes(int64_t c);
+int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* W, double* tau,
+                          char* scratch, unsigned* bar, unsigned* err, cudaStream_t st);
+int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st);
+
+int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us, double* Vs,
+                     unsigned* info, cudaStream_t st);
+
+}  // namespace rutv

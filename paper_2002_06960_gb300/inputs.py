@@ -15,6 +15,7 @@ the spectra below are the ones the workloads are defined with:
 * ``smooth``  sigma_j = 10^(-8 j / p)            (smooth decay over 8 decades)
 * ``step``    sigma_j = 1 for j < gap, else 1e-6 (gap = floor(p/10) unless given)
 * ``exp16``   sigma_j = exp(-j/16)               (batched workload)
+* ``linear``  sigma_j = 1 - j/(2p)               (well separated, no deep tail)
 
 with j = 0 .. p-1 and p = min(m, n).
 """
@@ -66,6 +67,8 @@ def spectrum(kind: str, p: int, gap: int | None = None) -> torch.Tensor:
         return torch.exp(-j / 16.0)
     if kind == "smooth":
         return torch.pow(10.0, -8.0 * j / p)
+    if kind == "linear":
+        return 1.0 - j / (2.0 * p)
     if kind == "step":
         g = p // 10 if gap is None else gap
         return torch.where(j < g, torch.ones_like(j), torch.full_like(j, 1e-6))
@@ -97,7 +100,7 @@ def batch_sizes(count: int, lo: int, hi: int, seed: int) -> list[tuple[int, int]
 
 
 def algorithmic_flops(m: int, n: int, b: int, q: int, want_u: bool = True,
-                      want_v: bool = True) -> float:
+                      want_v: bool = True, max_steps: int | None = None) -> float:
     """Leading-order flop count of one randUTV factorization, summed per step.
 
     Counted per step (k = offset, bi = block width, rm = m-k, rn = n-k):
@@ -106,11 +109,14 @@ def algorithmic_flops(m: int, n: int, b: int, q: int, want_u: bool = True,
     panel QRs 2 bi^2 (r - bi/3) + r bi^2 each; the fold of the small SVD
     2 bi^2 (k + rn - bi) + 2 bi^2 (m + n).  Steps that the method skips (no
     right transform when rn == bi, no left one when rm == bi) count nothing.
+    ``max_steps`` counts only the first that many block steps.
     """
     p = min(m, n)
     k = 0
     tot = 0.0
-    while k < p:
+    step = 0
+    while k < p and (max_steps is None or step < max_steps):
+        step += 1
         bi = min(b, p - k)
         rm, rn = m - k, n - k
         if rn > bi:
