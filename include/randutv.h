@@ -89,6 +89,33 @@ int randutv_factor_host(int64_t m, int64_t n, const double* A_host, int64_t lda,
 /* Status word of the last _ex call on `stream` (synchronizes the stream). */
 int randutv_stream_status(void* stream);
 
+/* ---------------------------------------------------------- mixed precision --
+ * The same block steps (§3.1, Fig. 2) with FP32 input and output, asynchronous
+ * on `stream` (arg 12); device errors are read with randutv_stream_status().
+ *   A (3)   m x n FP32, leading dimension lda (4); U (8), T (9), V (10) FP32
+ *           with ld m, m, n; U or V may be NULL.
+ *   b (5)   block size, a multiple of 8 in [8, 256].
+ *   max_steps (11) as in randutv_factor_ex.
+ * Arithmetic: T, U^T and V^T are held as three BF16 planes each (24
+ * significant bits, the precision of FP32 storage).  The sketch and power
+ * products take one BF16 product on the tensor cores (FP32 accumulation);
+ * every compact-WY update and the fold-back take the six-product BF16 split,
+ * which is FP32-accurate; the Householder vectors and norms, the WY factor S
+ * and the b x b SVD are FP64.  The sketch is RNE(bf16) of the FP64 sketch
+ * of randutv_philox_normal. */
+int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int b, int q,
+                         uint64_t seed, float* U, float* T, float* V, int max_steps,
+                         void* stream);
+
+/* Tensor-core GEMM of the mixed path, FP32 in and out:
+ * C = alpha op(A) B + beta C with op(A) = A (transa 'N', A is M x K, MN-major
+ * operand) or A^T (transa 'T', A is K x M, K-major operand), B K x N.  The
+ * operands are split into `planes` BF16 planes (1: one BF16 product; 3: the
+ * six products of the FP32-accurate split).  Asynchronous on `stream`. */
+int randutv_gemm_bf16(char transa, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                      int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                      int planes, void* stream);
+
 /* ------------------------------------------------------------ components --
  * The steps of one block, exposed so that each can be checked on its own.
  */

@@ -12,7 +12,8 @@ _BINDING_NAMES = (
     "randutv_philox_normal", "randutv_philox_words", "randutv_householder_qr",
     "randutv_wy_factor", "randutv_small_svd", "randutv_dgemm", "randutv_workspace_bytes",
     "randutv_finalize", "randutv_launch_count", "colmajor_empty", "to_colmajor", "lib",
-    "RandutvError", "exported_names", "randutv_profile_enable", "randutv_profile_read",
+    "RandutvError", "exported_names", "randutv_profile_enable", "randutv_profile_read", "randutv_factor_mixed",
+    "randutv_gemm_bf16",
 )
 
 

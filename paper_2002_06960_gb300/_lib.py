@@ -44,6 +44,10 @@ _SIGS = {
     "randutv_strerror": (ctypes.c_char_p, [c_int]),
     "randutv_last_error": (ctypes.c_char_p, []),
     "randutv_launch_count": (c_u64, [c_int]),
+    "randutv_factor_mixed": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_u64, c_vp, c_vp,
+                                     c_vp, c_int, c_vp]),
+    "randutv_gemm_bf16": (c_int, [ctypes.c_char, c_i64, c_i64, c_i64, ctypes.c_float, c_vp, c_i64,
+                                  c_vp, c_i64, ctypes.c_float, c_vp, c_i64, c_int, c_vp]),
     "randutv_profile_enable": (None, [c_int]),
     "randutv_profile_read": (c_int, [c_vp, c_int]),
     "randutv_profile_class_name": (ctypes.c_char_p, [c_int]),
@@ -272,3 +276,48 @@ def randutv_profile_read():
         out[name] = {"launches": int(buf[4 * c]), "ms": buf[4 * c + 1],
                      "flops": buf[4 * c + 2], "bytes": buf[4 * c + 3]}
     return out
+
+
+def _dev32(t, name):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != torch.float32:
+        raise ValueError(f"{name} must be float32")
+    return t
+
+
+def randutv_factor_mixed(A, b, q, seed, want_u=True, want_v=True, max_steps=-1, U=None, T=None,
+                         V=None):
+    """Mixed-precision randUTV on the current stream (FP32 column-major in/out).
+
+    Returns (U, T, V); call randutv_stream_status() to wait and read errors."""
+    m, n = A.shape
+    lda = _colmajor(_dev32(A, "A"), m, n, "A")
+    dev = A.device
+    if T is None:
+        T = colmajor_empty(m, n, device=dev, dtype=torch.float32)
+    if want_u and U is None:
+        U = colmajor_empty(m, m, device=dev, dtype=torch.float32)
+    if want_v and V is None:
+        V = colmajor_empty(n, n, device=dev, dtype=torch.float32)
+    for t, r, c, nm in ((T, m, n, "T"), (U, m, m, "U"), (V, n, n, "V")):
+        if t is not None and _colmajor(_dev32(t, nm), r, c, nm) != r:
+            raise ValueError(f"{nm} must have leading dimension {r}")
+    _check("randutv_factor_mixed", lib().randutv_factor_mixed(
+        m, n, _ptr(A), lda, b, q, seed, _ptr(U), _ptr(T), _ptr(V), max_steps, _stream()))
+    return U, T, V
+
+
+def randutv_gemm_bf16(transa, alpha, A, B, beta, C, planes=3):
+    """C = alpha op(A) B + beta C on the tensor cores (FP32 column-major CUDA tensors)."""
+    M, N = C.shape
+    K = A.shape[0] if transa == "T" else A.shape[1]
+    lda = _colmajor(_dev32(A, "A"), *A.shape, "A")
+    ldb = _colmajor(_dev32(B, "B"), *B.shape, "B")
+    ldc = _colmajor(_dev32(C, "C"), M, N, "C")
+    _check("randutv_gemm_bf16", lib().randutv_gemm_bf16(
+        transa.encode(), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(C), ldc, planes,
+        _stream()))
+    return C

@@ -1,0 +1,424 @@
+// Tensor-core GEMM for the mixed-precision path (tcgen05, TMEM, TMA).
+//
+//   C[M x N] (+)= alpha * sum_{(i,j) in pairs} op(A_i)[M x K] * B_j[K x N]
+//
+// A_i, B_j are BF16 "planes" of FP32-level matrices: X = X_0 + X_1 + X_2 with
+// X_0 = bf16(X), X_1 = bf16(X - X_0), X_2 = bf16(X - X_0 - X_1), 8 significant
+// bits each.  One plane gives a BF16 product (the sketch and power products
+// of §3.1, V-hat step 2); three planes with the six pairs i + j <= 2 give the
+// product to FP32 accuracy (the compact-WY updates of Fig. 2), with FP32
+// accumulation in tensor memory throughout.
+//
+// Operand layout (column-major sources, loaded by TMA with 128-byte swizzle):
+//   B is always K-major: B(k, n) = Y[k + n ldy] for a column-major Y.
+//   A is K-major when op(A) = X^T (A(m, k) = X[k + m ldx]) and MN-major when
+//   op(A) = X (A(m, k) = X[m + k ldx]); both are BF16 (kind::f16), for which
+//   the MMA takes either major-ness.
+// Tile 128 x 128 x 64, cta_group::1, accumulator 128 lanes x 128 FP32
+// columns of tensor memory.  Warp 0 issues TMA loads (and owns the TMEM
+// allocation), warp 1 issues the MMAs, warps 2-5 drain the accumulator.
+// Every mbarrier wait is bounded; on timeout the kernel records
+// RANDUTV_ETIMEOUT, lets its copies in flight land, frees TMEM and returns.
+#include <cstring>
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include "common.cuh"
+#include "mixed.h"
+
+namespace rutv {
+
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int THREADS = 192;
+constexpr int TILE_BYTES = BM * BK * 2;  // 16 KiB, also BN * BK * 2
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on the phase with the given parity; false (and err set) on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err,
+                                          unsigned site) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  unsigned spins = 0;
+  while (!mbar_try_wait(bar, parity)) {
+    if ((++spins & 255u) == 0) {
+      if (*(volatile unsigned*)err != 0) return false;
+      if (globaltimer_ns() - t0 > kWaitLimitNs) {
+        if (atomicCAS(err, 0u, (unsigned)RANDUTV_ETIMEOUT) == 0u) atomicExch(err + 1, site);
+        return false;
+      }
+    }
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
+                                            int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
+      "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor (sm_100 format): start address, leading
+// and stride byte offsets (all >> 4), version 1, 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version for sm_100
+  d |= (uint64_t)2 << 61;  // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, M = 128, N = 128.
+__device__ __forceinline__ uint32_t instr_desc(int a_mn_major) {
+  uint32_t d = 0;
+  d |= 1u << 4;                    // D format F32
+  d |= 1u << 7;                    // A format BF16
+  d |= 1u << 10;                   // B format BF16
+  d |= (uint32_t)a_mn_major << 15; // A major-ness (0 = K, 1 = MN)
+  d |= 0u << 16;                   // B K-major
+  d |= (uint32_t)(BN >> 3) << 17;  // N / 8
+  d |= (uint32_t)(BM >> 4) << 24;  // M / 16
+  return d;
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_u32(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
+      "%28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
+        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
+        "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+struct BgemmParams {
+  CUtensorMap ta[3];
+  CUtensorMap tb[3];
+  int M, N, K;
+  int na, nb, npairs;
+  int pair_a[6], pair_b[6];
+  int a_mn;            // A MN-major
+  int a_x0, a_y0;      // coordinate offsets of A's source (x = source row, y = source col)
+  int b_x0, b_y0;
+  int stages;
+  int mode;            // 0: C = alpha acc + beta C (FP32); 1: planes += alpha acc
+  float alpha, beta;
+  float* C;            // mode 0
+  int64_t ldc;
+  __nv_bfloat16* P0;   // mode 1 planes, same ld
+  __nv_bfloat16* P1;
+  __nv_bfloat16* P2;
+  int64_t ldp;
+  unsigned* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant__ BgemmParams p) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  // 1024-byte aligned tile area
+  uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int per_stage = (p.na + p.nb) * TILE_BYTES;
+  uint64_t* full = (uint64_t*)(smem + (size_t)p.stages * per_stage);
+  uint64_t* empty = full + p.stages;
+  uint64_t* acc_full = empty + p.stages;
+  uint64_t* mma_done = acc_full + 1;
+  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // N tiles vary fastest so the CTAs that share an A tile run together (L2 reuse)
+  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
+  const int ksteps = (p.K + BK - 1) / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < p.stages; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    mbar_init(acc_full, 1);
+    mbar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(BN));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      int issued = 0;
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int s = ks % p.stages;
+        const int round = ks / p.stages;
+        if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), p.err, 11)) break;
+        uint8_t* st = smem + (size_t)s * per_stage;
+        mbar_expect_tx(&full[s], (uint32_t)per_stage);
+        const int k0 = ks * BK;
+        for (int i = 0; i < p.na; ++i) {
+          uint8_t* dst = st + i * TILE_BYTES;
+          if (p.a_mn) {
+            tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + m0, p.a_y0 + k0);
+            tma_load_2d(dst + TILE_BYTES / 2, &p.ta[i], &full[s], p.a_x0 + m0 + 64, p.a_y0 + k0);
+          } else {
+            tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + k0, p.a_y0 + m0);
+          }
+        }
+        for (int j = 0; j < p.nb; ++j) {
+          uint8_t* dst = st + (p.na + j) * TILE_BYTES;
+          tma_load_2d(dst, &p.tb[j], &full[s], p.b_x0 + k0, p.b_y0 + n0);
+        }
+        issued = ks + 1;
+      }
+      // let every copy issued land before the CTA can exit
+      for (int ks = (issued > p.stages ? issued - p.stages : 0); ks < issued; ++ks) {
+        mbar_wait(&full[ks % p.stages], (uint32_t)((ks / p.stages) & 1), p.err, 12);
+      }
+    }
+  } else if (warp == 1) {
+    // ----------------------------------------------------------------- MMA
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(p.a_mn);
+      uint32_t accum = 0;
+      for (int ks = 0; ks < ksteps; ++ks) {
+        const int s = ks % p.stages;
+        if (!mbar_wait(&full[s], (uint32_t)((ks / p.stages) & 1), p.err, 13)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t st = smem_u32(smem + (size_t)s * per_stage);
+        for (int q = 0; q < p.npairs; ++q) {
+          const uint32_t a_addr = st + p.pair_a[q] * TILE_BYTES;
+          const uint32_t b_addr = st + (p.na + p.pair_b[q]) * TILE_BYTES;
+#pragma unroll
+          for (int kk = 0; kk < BK / 16; ++kk) {
+            uint64_t ad, bd;
+            if (p.a_mn) ad = smem_desc(a_addr + kk * 2048, TILE_BYTES / 2, 1024);
+            else        ad = smem_desc(a_addr + kk * 32, 16, 1024);
+            bd = smem_desc(b_addr + kk * 32, 16, 1024);
+            mma_bf16(tmem, ad, bd, idesc, accum);
+            accum = 1;
+          }
+        }
+        mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
+      }
+      mma_commit(acc_full);
+      mma_commit(mma_done);
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue
+    const int q = warp & 3;  // TMEM lane quadrant this warp may access
+    const bool ok = mbar_wait(acc_full, 0, p.err, 14);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok && *(volatile unsigned*)p.err == 0) {
+      const int row = m0 + q * 32 + lane;
+      for (int c = 0; c < BN; c += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (row < p.M) {
+          if (p.mode == 0) {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int col = n0 + c + i;
+              if (col < p.N) {
+                float* dst = p.C + (int64_t)row + (int64_t)col * p.ldc;
+                float r = p.alpha * v[i];
+                if (p.beta != 0.f) r = fmaf(p.beta, *dst, r);
+                *dst = r;
+              }
+            }
+          } else {
+#pragma unroll
+            for (int i = 0; i < 32; ++i) {
+              const int col = n0 + c + i;
+              if (col < p.N) {
+                const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
+                const float x = __bfloat162float(p.P0[o]) + __bfloat162float(p.P1[o]) +
+                                __bfloat162float(p.P2[o]);
+                const float y = fmaf(p.alpha, v[i], x);
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(y);
+                const float r1 = y - __bfloat162float(h0);
+                const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
+                const __nv_bfloat16 h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+                p.P0[o] = h0;
+                p.P1[o] = h1;
+                p.P2[o] = h2;
+              }
+            }
+          }
+        }
+      }
+    }
+  }
+
+  // teardown: all MMAs must have completed before TMEM is released
+  __syncthreads();
+  if (warp == 0) {
+    mbar_wait(mma_done, 0, p.err, 15);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+  }
+}
+
+// ---------------------------------------------------------------- host side
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+int get_encode() {
+  if (g_encode) return 0;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  RUTV_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                           cudaEnableDefault, &q));
+  if (q != cudaDriverEntryPointSuccess || !fn) return RANDUTV_ECUDA;
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return 0;
+}
+
+}  // namespace
+
+// Tensor map of a column-major BF16 matrix (rows x cols, ld elements), box
+// {64 rows, box_cols columns}, 128-byte swizzle.  ld must be a multiple of 8.
+int make_tmap_bf16(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols,
+                   int64_t ld, int box_cols) {
+  RUTV_TRY(get_encode());
+  if (((uintptr_t)base & 15) || (ld % 8) != 0) return RANDUTV_EUNSUPPORTED;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {64u, (cuuint32_t)box_cols};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled failed");
+    return RANDUTV_ECUDA;
+  }
+  return 0;
+}
+
+int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int K, int pairs_mode,
+                 const BgemmOut& out, unsigned* err, cudaStream_t st) {
+  if (M <= 0 || N <= 0) return 0;
+  BgemmParams p;
+  memset(&p, 0, sizeof p);
+  p.na = A.nplanes;
+  p.nb = B.nplanes;
+  for (int i = 0; i < p.na; ++i) {
+    // A K-major: source X (K rows x M cols), box {64 K, 128 M}
+    // A MN-major: source X (M rows x K cols), box {64 M, 64 K}
+    RUTV_TRY(make_tmap_bf16(&p.ta[i], A.planes[i], A.rows, A.cols, A.ld, A.mn_major ? 64 : 128));
+  }
+  for (int j = 0; j < p.nb; ++j) {
+    RUTV_TRY(make_tmap_bf16(&p.tb[j], B.planes[j], B.rows, B.cols, B.ld, 128));
+  }
+  p.M = M;
+  p.N = N;
+  p.K = K;
+  if (pairs_mode == 3 && p.na == 3 && p.nb == 3) {
+    const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
+    p.npairs = 6;
+    for (int i = 0; i < 6; ++i) { p.pair_a[i] = pa[i]; p.pair_b[i] = pb[i]; }
+  } else {
+    p.npairs = 1;
+    p.pair_a[0] = 0;
+    p.pair_b[0] = 0;
+    p.na = p.nb = 1;
+  }
+  p.a_mn = A.mn_major;
+  p.a_x0 = (int)A.x0;
+  p.a_y0 = (int)A.y0;
+  p.b_x0 = (int)B.x0;
+  p.b_y0 = (int)B.y0;
+  const int per_stage = (p.na + p.nb) * TILE_BYTES;
+  int stages = (200 * 1024) / per_stage;
+  if (stages > 6) stages = 6;
+  if (stages < 1) stages = 1;
+  p.stages = stages;
+  p.mode = out.mode;
+  p.alpha = out.alpha;
+  p.beta = out.beta;
+  p.C = out.C;
+  p.ldc = out.ldc;
+  p.P0 = out.planes[0];
+  p.P1 = out.planes[1];
+  p.P2 = out.planes[2];
+  p.ldp = out.ldp;
+  p.err = err;
+  const size_t smem = 1024 + (size_t)stages * per_stage + (2 * stages + 2) * 8 + 16;
+  static size_t configured = 0;
+  if (smem > configured) {
+    RUTV_CK(cudaFuncSetAttribute(bgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)smem));
+    configured = smem;
+  }
+  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  ProfScope prof(K_BGEMM, 2.0 * M * (double)N * K * p.npairs,
+                 2.0 * ((double)M * K * p.na + (double)K * N * p.nb) +
+                     (out.mode == 0 ? 4.0 : 12.0) * M * (double)N,
+                 st);
+  bgemm_kernel<<<grid, THREADS, smem, st>>>(p);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace rutv

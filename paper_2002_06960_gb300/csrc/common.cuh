@@ -19,13 +19,23 @@ int cuda_fail(cudaError_t e, const char* what);
     if (_e != cudaSuccess) return ::rutv::cuda_fail(_e, #call); \
   } while (0)
 
+#define RUTV_TRY(x)          \
+  do {                       \
+    int _r = (x);            \
+    if (_r != 0) return _r;  \
+  } while (0)
+
+// Records a message for randutv_last_error().
+void set_last_error(const char* msg);
+
 // Counts kernel launches (the library's own kernels only).
 void note_launch(int n = 1);
 
 // Per-kernel-class timing (tracing): when enabled, every launch of the
 // library is bracketed by a CUDA event pair on its stream and tagged with the
 // algorithmic flops and bytes of that launch.
-enum KernelClass { K_PHILOX = 0, K_DGEMM, K_QR, K_WY, K_SVD, K_OTHER, K_NCLASS };
+enum KernelClass { K_PHILOX = 0, K_DGEMM, K_QR, K_WY, K_SVD, K_OTHER, K_BGEMM, K_CONVERT,
+                   K_NCLASS };
 struct ProfScope {
   ProfScope(int cls, double flops, double bytes, cudaStream_t st);
   ~ProfScope();
@@ -53,6 +63,9 @@ struct Arena {
 };
 // Makes sure the device scratch holds at least `bytes`; returns status.
 int scratch_reserve(size_t bytes, Arena* out);
+
+// The device status words of the current device (64 words, persistent).
+int status_words(unsigned** out);
 
 // Words of device status shared by the kernels of one call: [0] error code,
 // [1] where the error happened, [2..3] barrier counter and generation.

@@ -1,0 +1,389 @@
+// Mixed-precision randUTV (the same block step as the FP64 path, §3.1 and
+// Fig. 2, with different arithmetic):
+//   * T, U^T and V^T are held as three BF16 planes each (FP32-level storage);
+//     U and V are kept transposed so that every update of them contracts
+//     over their row index, which is the K-major operand layout of the MMA.
+//   * Sketch and power products Y = T22^T G, Z = T22 Y: one BF16 product on
+//     tcgen05 (plane 0 of T is the BF16 shadow of T22), FP32 accumulation,
+//     with Y and Z rescaled by exact powers of two between products.
+//   * Every compact-WY update and the fold-back of the small SVD: the six-
+//     product BF16 split on tcgen05, FP32 accuracy, FP32 accumulation.
+//   * Householder vectors and norms (the panel QRs), the WY factor S and the
+//     b x b SVD: FP64, the same kernels as the FP64 path.
+#include <cuda_bf16.h>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "mixed.h"
+
+namespace rutv {
+
+namespace {
+
+__global__ void f32_to_f64_kernel(const float* __restrict__ src, int64_t lds, int64_t rows,
+                                  int64_t cols, double* __restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    dst[i + j * ldd] = (double)src[i + j * lds];
+  }
+}
+
+int grid_of(int64_t total) {
+  int64_t blocks = (total + 255) / 256;
+  const int64_t cap = (int64_t)dev_info().sms * 16;
+  if (blocks > cap) blocks = cap;
+  if (blocks < 1) blocks = 1;
+  return (int)blocks;
+}
+
+int f32_to_f64(const float* src, int64_t lds, int64_t rows, int64_t cols, double* dst, int64_t ldd,
+               cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return 0;
+  f32_to_f64_kernel<<<grid_of(rows * cols), 256, 0, st>>>(src, lds, rows, cols, dst, ldd);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
+// Operand from planes; rows x cols is the extent of the valid source (a
+// smaller leading block of a larger buffer), so that TMA zero-fills past it.
+BgemmOperand opnd(const Planes& P, int nplanes, int64_t x0, int64_t y0, int mn_major,
+                  int64_t rows = -1, int64_t cols = -1) {
+  BgemmOperand o;
+  for (int i = 0; i < 3; ++i) o.planes[i] = P.p[i];
+  o.nplanes = nplanes;
+  o.rows = rows < 0 ? P.rows : rows;
+  o.cols = cols < 0 ? P.cols : cols;
+  o.ld = P.ld;
+  o.x0 = x0;
+  o.y0 = y0;
+  o.mn_major = mn_major;
+  return o;
+}
+
+BgemmOperand opnd_bf16(const __nv_bfloat16* X, int64_t rows, int64_t cols, int64_t ld,
+                       int mn_major) {
+  BgemmOperand o;
+  o.planes[0] = X;
+  o.nplanes = 1;
+  o.rows = rows;
+  o.cols = cols;
+  o.ld = ld;
+  o.mn_major = mn_major;
+  return o;
+}
+
+BgemmOut out_f32(float* C, int64_t ldc, float alpha = 1.f, float beta = 0.f) {
+  BgemmOut o;
+  o.mode = 0;
+  o.C = C;
+  o.ldc = ldc;
+  o.alpha = alpha;
+  o.beta = beta;
+  return o;
+}
+
+BgemmOut out_planes(const Planes& P, int64_t r0, int64_t c0, float alpha) {
+  BgemmOut o;
+  o.mode = 1;
+  o.alpha = alpha;
+  for (int i = 0; i < 3; ++i) o.planes[i] = P.at(i, r0, c0);
+  o.ldp = P.ld;
+  return o;
+}
+
+struct MixedWork {
+  Planes T, Ut, Vt;             // m x n, m x m (U^T), n x n (V^T)
+  Planes W, WSt, Xp, Sp, Us, Vs; // small operands as planes
+  __nv_bfloat16 *G, *Yb;        // BF16 sketch operands
+  float *Y, *Z, *X, *tmp, *Gram32, *scal;
+  double *Y64, *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64, *WS64;
+  char* qr;
+  double* dgemm;
+  size_t dgemm_bytes;
+};
+
+size_t planes_bytes(int64_t rows, int64_t cols) {
+  return 3 * (size_t)pad8(rows) * (size_t)cols * sizeof(__nv_bfloat16) + 3 * 256;
+}
+
+Planes carve_planes(Arena& ar, int64_t rows, int64_t cols) {
+  Planes P;
+  P.rows = rows;
+  P.cols = cols;
+  P.ld = pad8(rows);
+  for (int i = 0; i < 3; ++i)
+    P.p[i] = (__nv_bfloat16*)ar.take((size_t)P.ld * (size_t)cols * sizeof(__nv_bfloat16));
+  return P;
+}
+
+size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
+  const int64_t big = m > n ? m : n;
+  size_t s = 0;
+  auto add = [&](size_t x) { s += (x + 255) & ~size_t(255); };
+  add(planes_bytes(m, n));
+  add(planes_bytes(m, m));
+  add(planes_bytes(n, n));
+  add(planes_bytes(big, b));      // W
+  add(planes_bytes(b, big));      // WSt
+  add(planes_bytes(b, big));      // Xp (X^T or Xv/Xl)
+  add(planes_bytes(b, b));        // Sp (S^T)
+  add(planes_bytes(b, b));        // Us
+  add(planes_bytes(b, b));        // Vs
+  add((size_t)pad8(big) * b * 2); // G
+  add((size_t)pad8(big) * b * 2); // Yb
+  for (int i = 0; i < 4; ++i) add((size_t)big * b * 4);  // Y, Z, X, tmp
+  add((size_t)b * b * 4 + 256);   // Gram32
+  add(256);                       // scal
+  for (int i = 0; i < 3; ++i) add((size_t)big * b * 8);  // Y64, W64, WS64
+  add((size_t)b * 8 * 2);         // tau, D
+  for (int i = 0; i < 5; ++i) add((size_t)b * b * 8);    // Gram64, S64, Us64, Vs64, blk64
+  add(householder_scratch_bytes(b));
+  add(dgemm_scratch_bytes(b, b));
+  return s + 8192;
+}
+
+MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
+  const int64_t big = m > n ? m : n;
+  MixedWork w;
+  w.T = carve_planes(ar, m, n);
+  w.Ut = carve_planes(ar, m, m);
+  w.Vt = carve_planes(ar, n, n);
+  w.W = carve_planes(ar, big, b);
+  w.WSt = carve_planes(ar, b, big);
+  w.Xp = carve_planes(ar, b, big);
+  w.Sp = carve_planes(ar, b, b);
+  w.Us = carve_planes(ar, b, b);
+  w.Vs = carve_planes(ar, b, b);
+  w.G = (__nv_bfloat16*)ar.take((size_t)pad8(big) * b * 2);
+  w.Yb = (__nv_bfloat16*)ar.take((size_t)pad8(big) * b * 2);
+  w.Y = (float*)ar.take((size_t)big * b * 4);
+  w.Z = (float*)ar.take((size_t)big * b * 4);
+  w.X = (float*)ar.take((size_t)big * b * 4);
+  w.tmp = (float*)ar.take((size_t)big * b * 4);
+  w.Gram32 = (float*)ar.take((size_t)b * b * 4 + 256);
+  w.scal = (float*)ar.take(256);
+  w.Y64 = (double*)ar.take((size_t)big * b * 8);
+  w.W64 = (double*)ar.take((size_t)big * b * 8);
+  w.WS64 = (double*)ar.take((size_t)big * b * 8);
+  w.tau = (double*)ar.take((size_t)b * 8);
+  w.D = (double*)ar.take((size_t)b * 8);
+  w.Gram64 = (double*)ar.take((size_t)b * b * 8);
+  w.S64 = (double*)ar.take((size_t)b * b * 8);
+  w.Us64 = (double*)ar.take((size_t)b * b * 8);
+  w.Vs64 = (double*)ar.take((size_t)b * b * 8);
+  w.blk64 = (double*)ar.take((size_t)b * b * 8);
+  w.qr = (char*)ar.take(householder_scratch_bytes(b));
+  w.dgemm_bytes = dgemm_scratch_bytes(b, b);
+  w.dgemm = (double*)ar.take(w.dgemm_bytes);
+  return w;
+}
+
+struct MCtx {
+  int64_t m, n;
+  int b, q;
+  uint64_t seed;
+  bool want_u, want_v;
+  MixedWork w;
+  unsigned* status;
+  cudaStream_t st;
+};
+
+// From the FP64 reflectors W64 (r x bi) and tau: W planes, S (FP64), and
+// WSt = (W S^T)^T as planes (bi x r).
+int mixed_wy(MCtx& c, int64_t r, int64_t bi) {
+  MixedWork& w = c.w;
+  RUTV_TRY(split_f64(w.W64, r, r, bi, 0, w.W, 0, 0, c.st));
+  // Gram = W^T W to FP32 accuracy, then S in FP64
+  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, bi), opnd(w.W, 3, 0, 0, 0, r, bi), (int)bi, (int)bi, (int)r, 3,
+                        out_f32(w.Gram32, bi), c.status, c.st));
+  RUTV_TRY(f32_to_f64(w.Gram32, bi, bi, bi, w.Gram64, bi, c.st));
+  RUTV_TRY(launch_wy_factor(bi, w.Gram64, w.tau, w.S64, c.st));
+  // WS = W S^T (r x bi): A = W (MN-major), B = S^T held as planes of S^T
+  RUTV_TRY(split_f64(w.S64, bi, bi, bi, 1, w.Sp, 0, 0, c.st));
+  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 1, r, bi), opnd(w.Sp, 3, 0, 0, 0, bi, bi), (int)r, (int)bi, (int)bi, 3,
+                        out_f32(w.tmp, r), c.status, c.st));
+  RUTV_TRY(split_f32(w.tmp, r, bi, r, 1, w.WSt, 0, 0, c.st));
+  return 0;
+}
+
+// X <- X - (X_in W) (W S^T)^T for a transposed factor Xt (rows k: of U^T or V^T):
+// Xt(k:, :) <- Xt(k:, :) - WS (W^T Xt(k:, :)).
+int mixed_apply_transposed(MCtx& c, const Planes& Xt, int64_t k, int64_t r, int64_t bi) {
+  MixedWork& w = c.w;
+  const int64_t cols = Xt.cols;
+  // Xv = W^T Xt(k:, :)   (bi x cols)
+  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, bi), opnd(Xt, 3, k, 0, 0), (int)bi, (int)cols, (int)r, 3,
+                        out_f32(w.X, bi), c.status, c.st));
+  RUTV_TRY(split_f32(w.X, bi, bi, cols, 0, w.Xp, 0, 0, c.st));
+  // Xt(k:, :) -= WS Xv   (A = WS via its transpose planes, K-major)
+  RUTV_TRY(launch_bgemm(opnd(w.WSt, 3, 0, 0, 0, bi, r), opnd(w.Xp, 3, 0, 0, 0, bi, cols), (int)r, (int)cols,
+                        (int)bi, 3, out_planes(Xt, k, 0, -1.f), c.status, c.st));
+  return 0;
+}
+
+int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
+  const int64_t m = c.m, n = c.n, rm = m - k, rn = n - k;
+  MixedWork& w = c.w;
+  // ---------------- right transform
+  if (rn > bi) {
+    RUTV_TRY(philox_normal_bf16(c.seed, (uint32_t)step, 0u, 0u, rm, bi, w.G, pad8(rm), c.st));
+    // Y = T22^T G   (plane 0 of T is the BF16 copy of T22)
+    RUTV_TRY(launch_bgemm(opnd(w.T, 1, k, k, 0), opnd_bf16(w.G, rm, bi, pad8(rm), 0), (int)rn,
+                          (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st));
+    for (int it = 0; it < c.q; ++it) {
+      RUTV_TRY(scaled_bf16(w.Y, rn, rn, bi, w.Yb, pad8(rn), w.scal, c.st));
+      RUTV_TRY(launch_bgemm(opnd(w.T, 1, k, k, 1), opnd_bf16(w.Yb, rn, bi, pad8(rn), 0), (int)rm,
+                            (int)bi, (int)rn, 1, out_f32(w.Z, rm), c.status, c.st));
+      RUTV_TRY(scaled_bf16(w.Z, rm, rm, bi, w.Yb, pad8(rm), w.scal, c.st));
+      RUTV_TRY(launch_bgemm(opnd(w.T, 1, k, k, 0), opnd_bf16(w.Yb, rm, bi, pad8(rm), 0), (int)rn,
+                            (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st));
+    }
+    RUTV_TRY(f32_to_f64(w.Y, rn, rn, bi, w.Y64, rn, c.st));
+    RUTV_TRY(launch_householder_qr(rn, bi, w.Y64, rn, w.W64, w.tau, w.qr, c.status + 2, c.status,
+                                   c.st));
+    RUTV_TRY(mixed_wy(c, rn, bi));
+    // X = T(:, k:) W (m x bi), then T(:, k:) -= X WS^T with X^T as planes
+    RUTV_TRY(launch_bgemm(opnd(w.T, 3, 0, k, 1), opnd(w.W, 3, 0, 0, 0, rn, bi), (int)m, (int)bi, (int)rn, 3,
+                          out_f32(w.X, m), c.status, c.st));
+    RUTV_TRY(split_f32(w.X, m, bi, m, 1, w.Xp, 0, 0, c.st));
+    RUTV_TRY(launch_bgemm(opnd(w.Xp, 3, 0, 0, 0, bi, m), opnd(w.WSt, 3, 0, 0, 0, bi, rn), (int)m, (int)rn, (int)bi,
+                          3, out_planes(w.T, 0, k, -1.f), c.status, c.st));
+    if (c.want_v) RUTV_TRY(mixed_apply_transposed(c, w.Vt, k, rn, bi));
+  }
+  // ---------------- left transform
+  if (rm > bi) {
+    RUTV_TRY(merge_f64(w.T, k, k, rm, bi, 0, w.Y64, rm, c.st));
+    RUTV_TRY(launch_householder_qr(rm, bi, w.Y64, rm, w.W64, w.tau, w.qr, c.status + 2, c.status,
+                                   c.st));
+    RUTV_TRY(split_f64(w.Y64, rm, rm, bi, 0, w.T, k, k, c.st));  // R and exact zeros
+    RUTV_TRY(mixed_wy(c, rm, bi));
+    if (rn > bi) {
+      const int64_t nc = rn - bi;
+      RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, rm, bi), opnd(w.T, 3, k, k + bi, 0), (int)bi, (int)nc,
+                            (int)rm, 3, out_f32(w.X, bi), c.status, c.st));
+      RUTV_TRY(split_f32(w.X, bi, bi, nc, 0, w.Xp, 0, 0, c.st));
+      RUTV_TRY(launch_bgemm(opnd(w.WSt, 3, 0, 0, 0, bi, rm), opnd(w.Xp, 3, 0, 0, 0, bi, nc), (int)rm, (int)nc,
+                            (int)bi, 3, out_planes(w.T, k, k + bi, -1.f), c.status, c.st));
+    }
+    if (c.want_u) RUTV_TRY(mixed_apply_transposed(c, w.Ut, k, rm, bi));
+  }
+  // ---------------- small SVD (FP64) and fold-back (six-product BF16)
+  RUTV_TRY(merge_f64(w.T, k, k, bi, bi, 0, w.blk64, bi, c.st));
+  RUTV_TRY(launch_small_svd((int)bi, w.blk64, bi, w.D, w.Us64, w.Vs64, c.status + 8, c.st));
+  RUTV_TRY(split_f64(w.Us64, bi, bi, bi, 0, w.Us, 0, 0, c.st));
+  RUTV_TRY(split_f64(w.Vs64, bi, bi, bi, 0, w.Vs, 0, 0, c.st));
+  if (k > 0) {  // T(0:k, blk) <- T(0:k, blk) Vs
+    RUTV_TRY(launch_bgemm(opnd(w.T, 3, 0, k, 1), opnd(w.Vs, 3, 0, 0, 0, bi, bi), (int)k, (int)bi, (int)bi, 3,
+                          out_f32(w.tmp, k), c.status, c.st));
+    RUTV_TRY(split_f32(w.tmp, k, k, bi, 0, w.T, 0, k, c.st));
+  }
+  if (rn > bi) {  // T(blk, k+bi:) <- Us^T T(blk, k+bi:)
+    const int64_t nc = rn - bi;
+    RUTV_TRY(launch_bgemm(opnd(w.Us, 3, 0, 0, 0, bi, bi), opnd(w.T, 3, k, k + bi, 0), (int)bi, (int)nc,
+                          (int)bi, 3, out_f32(w.tmp, bi), c.status, c.st));
+    RUTV_TRY(split_f32(w.tmp, bi, bi, nc, 0, w.T, k, k + bi, c.st));
+  }
+  if (c.want_v) {  // V(:, blk) <- V(:, blk) Vs, i.e. V^T(blk, :) <- Vs^T V^T(blk, :)
+    RUTV_TRY(launch_bgemm(opnd(w.Vs, 3, 0, 0, 0, bi, bi), opnd(w.Vt, 3, k, 0, 0), (int)bi, (int)n, (int)bi,
+                          3, out_f32(w.tmp, bi), c.status, c.st));
+    RUTV_TRY(split_f32(w.tmp, bi, bi, n, 0, w.Vt, k, 0, c.st));
+  }
+  if (c.want_u) {
+    RUTV_TRY(launch_bgemm(opnd(w.Us, 3, 0, 0, 0, bi, bi), opnd(w.Ut, 3, k, 0, 0), (int)bi, (int)m, (int)bi,
+                          3, out_f32(w.tmp, bi), c.status, c.st));
+    RUTV_TRY(split_f32(w.tmp, bi, bi, m, 0, w.Ut, k, 0, c.st));
+  }
+  RUTV_TRY(set_diag_planes(w.T, k, bi, w.D, c.st));
+  return 0;
+}
+
+}  // namespace
+
+size_t mixed_workspace_bytes(int64_t m, int64_t n, int64_t b) { return mixed_bytes(m, n, b); }
+
+}  // namespace rutv
+
+using namespace rutv;
+
+extern "C" {
+
+int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int b, int q,
+                         uint64_t seed, float* U, float* T, float* V, int max_steps, void* stream) {
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (!A) return -3;
+  if (lda < m) return -4;
+  if (b < 8 || b > 256 || (b % 8) != 0) return -5;
+  if (q < 0 || q > 16) return -6;
+  if (!T) return -9;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t p = m < n ? m : n;
+  const int64_t bb = b < p ? b : p;
+  if ((bb % 8) != 0 && bb != p) return -5;
+  Arena ar;
+  RUTV_TRY(scratch_reserve(mixed_bytes(m, n, b), &ar));
+  unsigned* status = nullptr;
+  RUTV_TRY(status_words(&status));
+  RUTV_CK(cudaMemsetAsync(status, 0, 64 * sizeof(unsigned), st));
+  MCtx c;
+  c.m = m;
+  c.n = n;
+  c.b = b;
+  c.q = q;
+  c.seed = seed;
+  c.want_u = U != nullptr;
+  c.want_v = V != nullptr;
+  c.w = carve_mixed(ar, m, n, b);
+  c.status = status;
+  c.st = st;
+  RUTV_TRY(launch_check_finite_f32(m, n, A, lda, status, st));
+  RUTV_TRY(split_f32(A, lda, m, n, 0, c.w.T, 0, 0, st));
+  if (c.want_u) RUTV_TRY(set_identity_planes(c.w.Ut, st));
+  if (c.want_v) RUTV_TRY(set_identity_planes(c.w.Vt, st));
+  int step = 0;
+  for (int64_t k = 0; k < p; k += b, ++step) {
+    const int64_t bi = (b < p - k) ? b : p - k;
+    if (max_steps >= 0 && step >= max_steps) break;
+    RUTV_TRY(mixed_step(c, step, k, bi));
+  }
+  RUTV_TRY(merge_f32(c.w.T, 0, 0, m, n, 0, T, m, st));
+  if (c.want_u) RUTV_TRY(merge_f32(c.w.Ut, 0, 0, m, m, 1, U, m, st));
+  if (c.want_v) RUTV_TRY(merge_f32(c.w.Vt, 0, 0, n, n, 1, V, n, st));
+  return 0;
+}
+
+int randutv_gemm_bf16(char transa, int64_t M, int64_t N, int64_t K, float alpha, const float* A,
+                      int64_t lda, const float* B, int64_t ldb, float beta, float* C, int64_t ldc,
+                      int planes, void* stream) {
+  const bool ta = (transa == 'T' || transa == 't');
+  if (!ta && !(transa == 'N' || transa == 'n')) return -1;
+  if (M < 1) return -2;
+  if (N < 1) return -3;
+  if (K < 1) return -4;
+  if (!A) return -6;
+  if (lda < (ta ? K : M)) return -7;
+  if (!B) return -8;
+  if (ldb < K) return -9;
+  if (!C) return -11;
+  if (ldc < M) return -12;
+  if (planes != 1 && planes != 3) return -13;
+  if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return RANDUTV_EUNSUPPORTED;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t ar_rows = ta ? K : M, ar_cols = ta ? M : K;
+  Arena ar;
+  RUTV_TRY(scratch_reserve(planes_bytes(ar_rows, ar_cols) + planes_bytes(K, N) + 4096, &ar));
+  unsigned* status = nullptr;
+  RUTV_TRY(status_words(&status));
+  RUTV_CK(cudaMemsetAsync(status, 0, 64 * sizeof(unsigned), st));
+  Planes Pa = carve_planes(ar, ar_rows, ar_cols);
+  Planes Pb = carve_planes(ar, K, N);
+  RUTV_TRY(split_f32(A, lda, ar_rows, ar_cols, 0, Pa, 0, 0, st));
+  RUTV_TRY(split_f32(B, ldb, K, N, 0, Pb, 0, 0, st));
+  return launch_bgemm(opnd(Pa, planes, 0, 0, ta ? 0 : 1), opnd(Pb, planes, 0, 0, 0), (int)M,
+                      (int)N, (int)K, planes, out_f32(C, ldc, alpha, beta), status, st);
+}
+
+}  // extern "C"

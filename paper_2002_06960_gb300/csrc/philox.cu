@@ -100,3 +100,42 @@ int launch_philox_words(uint64_t seed, uint4 c, int64_t count, uint32_t* out, cu
 }
 
 }  // namespace rutv
+
+// ---- BF16 sketch for the mixed-precision path: RNE(bf16) of the same FP64 normals.
+#include <cuda_bf16.h>
+
+namespace rutv {
+
+__global__ void philox_normal_bf16_kernel(PhiloxKey key, uint32_t step, uint32_t mid, uint32_t sid,
+                                          int64_t rows, int64_t count, __nv_bfloat16* G,
+                                          int64_t ldg) {
+  const int64_t npairs = (count + 1) >> 1;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npairs;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)p, step, mid, sid), key);
+    double z0, z1;
+    box_muller(w, &z0, &z1);
+    const int64_t l0 = 2 * p;
+    G[(l0 % rows) + (l0 / rows) * ldg] = __double2bfloat16(z0);
+    if (l0 + 1 < count) G[((l0 + 1) % rows) + ((l0 + 1) / rows) * ldg] = __double2bfloat16(z1);
+  }
+}
+
+int philox_normal_bf16(uint64_t seed, uint32_t step, uint32_t mid, uint32_t sid, int64_t rows,
+                       int64_t cols, __nv_bfloat16* G, int64_t ldg, cudaStream_t st) {
+  const int64_t count = rows * cols;
+  if (count == 0) return 0;
+  const int64_t npairs = (count + 1) >> 1;
+  int64_t blocks = (npairs + 255) / 256;
+  const int64_t cap = (int64_t)dev_info().sms * 16;
+  if (blocks > cap) blocks = cap;
+  PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
+  ProfScope prof(K_PHILOX, 0.0, 2.0 * (double)count, st);
+  philox_normal_bf16_kernel<<<(unsigned)blocks, 256, 0, st>>>(key, step, mid, sid, rows, count, G,
+                                                              ldg);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
+}  // namespace rutv

@@ -35,6 +35,8 @@ namespace rutv {
 static thread_local char g_last_error[512] = "";
 static std::atomic<uint64_t> g_launches{0};
 
+void set_last_error(const char* msg) { snprintf(g_last_error, sizeof g_last_error, "%s", msg); }
+
 int cuda_fail(cudaError_t e, const char* what) {
   snprintf(g_last_error, sizeof g_last_error, "%s: %s (%s)", what, cudaGetErrorName(e),
            cudaGetErrorString(e));
@@ -110,7 +112,7 @@ const DevInfo& dev_info() {
   return g_info[d];
 }
 
-static int status_words(unsigned** out) {
+int status_words(unsigned** out) {
   const int d = current_device();
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_scr[d].status) {
@@ -318,12 +320,6 @@ struct Ctx {
   cudaStream_t st;
 };
 
-#define RUTV_TRY(x)          \
-  do {                       \
-    int _r = (x);            \
-    if (_r != 0) return _r;  \
-  } while (0)
-
 int gemm(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
          int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc) {
   return launch_dgemm(ta, tb, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, c.w.gemm,
@@ -466,7 +462,8 @@ int randutv_profile_read(double* out, int nclass) {
 
 const char* randutv_profile_class_name(int cls) {
   static const char* names[K_NCLASS] = {"philox_normal", "dgemm", "householder_panel",
-                                        "wy_factor", "jacobi_svd", "other"};
+                                        "wy_factor", "jacobi_svd", "other", "bgemm_tcgen05",
+                                        "convert"};
   return (cls >= 0 && cls < K_NCLASS) ? names[cls] : "?";
 }
 

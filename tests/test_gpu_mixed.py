@@ -1,0 +1,96 @@
+"""Mixed-precision path: the tcgen05 GEMM and the whole factorization.
+
+The GEMM is checked against an FP64 product of the same operands: with one
+BF16 plane, against the product of the BF16-rounded inputs (so only the FP32
+accumulation differs); with three planes, against the exact product (the
+split is FP32-accurate).  The factorization is checked by its errors against
+the FP64 oracle: reconstruction, orthogonality, exact zeros, and the
+diagonal of T (the singular-value estimates).
+"""
+import pytest
+import torch
+
+import oracle
+from paper_2002_06960_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+f32, f64 = torch.float32, torch.float64
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2002_06960_gb300 import build
+    build.build()
+    import paper_2002_06960_gb300 as p
+    p.lib()
+    return p
+
+
+def colmajor(p, X):
+    return p.to_colmajor(X.to(f32), "cuda")
+
+
+@pytest.mark.parametrize("transa", ["T", "N"])
+@pytest.mark.parametrize("M,N,K", [(128, 128, 64), (200, 150, 300), (333, 256, 1000), (64, 40, 70),
+                                   (1, 1, 1), (1030, 130, 4097)])
+def test_bgemm_three_planes_is_fp32_accurate(pkg, transa, M, N, K):
+    g = torch.Generator().manual_seed(M + 7 * N + K)
+    A = torch.randn((K, M) if transa == "T" else (M, K), generator=g, dtype=f64).to(f32)
+    B = torch.randn(K, N, generator=g, dtype=f64).to(f32)
+    C = torch.randn(M, N, generator=g, dtype=f64).to(f32)
+    ref = 0.5 * ((A.double().T if transa == "T" else A.double()) @ B.double()) - 2.0 * C.double()
+    Cd = colmajor(pkg, C)
+    pkg.randutv_gemm_bf16(transa, 0.5, colmajor(pkg, A), colmajor(pkg, B), -2.0, Cd, planes=3)
+    torch.cuda.synchronize()
+    err = (Cd.cpu().double() - ref).abs().max().item()
+    scale = (A.double().abs().max() * B.double().abs().max() * K ** 0.5).item() + 2.0
+    assert err <= 2e-6 * scale, (err, scale)
+
+
+@pytest.mark.parametrize("transa", ["T", "N"])
+@pytest.mark.parametrize("M,N,K", [(256, 256, 512), (130, 70, 65), (512, 128, 2048)])
+def test_bgemm_one_plane_is_the_bf16_product(pkg, transa, M, N, K):
+    g = torch.Generator().manual_seed(M * 3 + N + K)
+    A = torch.randn((K, M) if transa == "T" else (M, K), generator=g, dtype=f64).to(f32)
+    B = torch.randn(K, N, generator=g, dtype=f64).to(f32)
+    Ab = A.to(torch.bfloat16).double()
+    Bb = B.to(torch.bfloat16).double()
+    ref = (Ab.T if transa == "T" else Ab) @ Bb
+    Cd = colmajor(pkg, torch.zeros(M, N))
+    pkg.randutv_gemm_bf16(transa, 1.0, colmajor(pkg, A), colmajor(pkg, B), 0.0, Cd, planes=1)
+    torch.cuda.synchronize()
+    err = (Cd.cpu().double() - ref).abs().max().item()
+    assert err <= 1e-5 * (K ** 0.5) * 4, err
+
+
+def _mixed(pkg, A, b, q, seed):
+    U, T, V = pkg.randutv_factor_mixed(colmajor(pkg, A), b, q, seed)
+    assert pkg.randutv_stream_status() == 0
+    return U.cpu().double(), T.cpu().double(), V.cpu().double()
+
+
+@pytest.mark.parametrize("kind,m,n,b,q", [("exp40", 512, 512, 64, 1), ("smooth", 1024, 1024, 256, 2),
+                                          ("smooth", 768, 512, 128, 2), ("smooth", 512, 768, 128, 1),
+                                          ("gauss", 300, 260, 64, 1)])
+def test_mixed_factorization_errors(pkg, kind, m, n, b, q):
+    A = inputs.matrix(kind, m, n, seed=1)
+    U, T, V = _mixed(pkg, A, b, q, 0)
+    recon = oracle.recon_error(A, U, T, V)
+    ou, ov = oracle.orth_error(U), oracle.orth_error(V)
+    assert recon < 1e-5, recon
+    assert ou < 1e-5 and ov < 1e-5, (ou, ov)
+    assert float(torch.tril(T, -1).abs().max()) == 0.0
+    ref = oracle.randutv(A, b, q, 0)
+    d, d0 = torch.diagonal(T).abs(), torch.diagonal(ref.T).abs()
+    # the leading singular-value estimates agree with the FP64 oracle's
+    top = d0 > 1e-4 * d0.max()
+    assert float(((d - d0).abs() / d0)[top].max()) < 1e-2
+
+
+def test_mixed_single_block_is_svd(pkg):
+    """b >= min(m, n): T = diag(sigma) of the prescribed spectrum, to FP32 accuracy."""
+    sig = torch.exp(-torch.arange(96, dtype=f64) / 20.0)
+    A = inputs.prescribed(96, 96, sig, seed=2)
+    U, T, V = _mixed(pkg, A, 128, 1, 0)
+    assert torch.allclose(torch.diagonal(T), sig, rtol=1e-5, atol=1e-6)
