@@ -146,6 +146,31 @@ int randutv_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, u
 int randutv_householder_qr(int64_t r, int64_t c, double* panel, int64_t ld, double* W,
                            double* tau, void* stream);
 
+/* randutv_householder_qr without any memory allocation (the paper has no
+ * counterpart; this is a service to callers).
+ * Some callers cannot allocate device memory at all: code running while a
+ * CUDA graph is being captured, where cudaMalloc is not allowed; programs
+ * that hand every byte of the GPU to their own allocator or memory pool; and
+ * real-time loops that cannot afford an allocation's latency or failure.
+ * This entry point serves them: it calls no cudaMalloc, cudaFree or other
+ * allocating routine.  Its scratch is a fixed array inside the library
+ * (about 386 KiB: partial sums for up to 192 SMs x 256 columns, plus its
+ * barrier and status words), which every GPU that loads the library holds
+ * until the process exits.
+ *   Arguments, layout and results are those of randutv_householder_qr; the
+ *   caller still owns panel, W and tau.
+ *   c > 256, or a device with more than 192 SMs: returns
+ *   RANDUTV_EUNSUPPORTED without launching anything.
+ *   The call is synchronous: it waits for the kernel on `stream` and returns
+ *   its device status (RANDUTV_ETIMEOUT if a bounded wait ran out).
+ *   The first call on a device looks up the array's device address (once
+ *   per device, with that device current); make that first call before any
+ *   stream capture.
+ *   All calls share the one array, so calls that overlap on the GPU (other
+ *   streams, other host threads) race and must be serialized by the caller. */
+int randutv_householder_qr_noalloc(int64_t r, int64_t c, double* panel, int64_t ld, double* W,
+                                   double* tau, void* stream);
+
 /* Compact-WY factor (Fig. 2: T_V, T_U): S (c x c, ld c, upper triangular)
  * with H_1 ... H_c = I - W S W^T, for W (r x c, ld r) and tau from
  * randutv_householder_qr. */

@@ -178,3 +178,92 @@ int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, 
 }
 
 }  // namespace rutv
+
+// ---------------------------------------------------------------------------
+// Householder QR without any allocation.
+//
+// The panel QR above needs scratch in global memory: the per-CTA partial sums
+// (SMs x (c + 1) doubles) and the words of its grid barrier and status.  The
+// library normally takes these from its own growing scratch, which it
+// allocates with cudaMalloc on first use.  This variant keeps them in one
+// fixed array in the library's device image instead, sized for at most
+// kNoAllocMaxSms SMs and kNoAllocMaxCols columns (about 386 KiB).  Every GPU
+// that loads the library holds that array until the process exits.
+#include <mutex>
+
+namespace rutv {
+namespace {
+
+constexpr int kNoAllocMaxSms = 192;
+constexpr int kNoAllocMaxCols = 256;
+constexpr size_t kNoAllocPartials = (size_t)kNoAllocMaxSms * (1 + kNoAllocMaxCols);
+constexpr size_t kNoAllocBytes = kNoAllocPartials * sizeof(double) + 256;
+
+// Partials first, then 64 status words: [0] error, [1] site, [2..3] barrier.
+static __device__ __align__(256) unsigned char g_qr_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mu;
+char* g_noalloc_ptr[64] = {nullptr};
+
+// Device address of the array on the current device; the host-side symbol
+// is only a stand-in and must never reach a kernel.  Looked up once per
+// device, with that device current.
+int noalloc_scratch(char** out) {
+  int dev = 0;
+  RUTV_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RANDUTV_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    RUTV_CK(cudaGetSymbolAddress(&p, g_qr_noalloc_scratch));
+    g_noalloc_ptr[dev] = (char*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return 0;
+}
+
+}  // namespace
+}  // namespace rutv
+
+extern "C" int randutv_householder_qr_noalloc(int64_t r, int64_t c, double* panel, int64_t ld,
+                                              double* W, double* tau, void* stream) {
+  using namespace rutv;
+  if (r < 1) return -1;
+  if (c < 1 || c > r) return -2;
+  if (!panel) return -3;
+  if (ld < r) return -4;
+  if (!W) return -5;
+  if (!tau) return -6;
+  if (c > kNoAllocMaxCols) {
+    set_last_error("randutv_householder_qr_noalloc: more than 256 columns");
+    return RANDUTV_EUNSUPPORTED;
+  }
+  const int sms = dev_info().sms;
+  if (sms > kNoAllocMaxSms) {
+    set_last_error("randutv_householder_qr_noalloc: device has more than 192 SMs");
+    return RANDUTV_EUNSUPPORTED;
+  }
+  char* base = nullptr;
+  RUTV_TRY(noalloc_scratch(&base));
+  unsigned* words = (unsigned*)(base + kNoAllocPartials * sizeof(double));
+  cudaStream_t st = (cudaStream_t)stream;
+  // error, site and barrier words start at zero; the partials are always
+  // written before they are read
+  RUTV_CK(cudaMemsetAsync(words, 0, 4 * sizeof(unsigned), st));
+  int nb = (int)((r + 63) / 64);
+  if (nb > sms) nb = sms;
+  QrArgs a;
+  a.r = r; a.c = c; a.A = panel; a.lda = ld; a.W = W; a.tau = tau;
+  a.part1 = (double*)base;
+  a.part2 = a.part1 + sms;
+  a.bar = words + 2;
+  a.err = words;
+  void* args[] = {&a};
+  RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel, dim3(nb),
+                                      dim3(QR_THREADS), args, 0, st));
+  note_launch();
+  unsigned h[2] = {0, 0};
+  RUTV_CK(cudaMemcpyAsync(h, words, sizeof h, cudaMemcpyDeviceToHost, st));
+  RUTV_CK(cudaStreamSynchronize(st));
+  return (int)h[0];
+}
