@@ -35,6 +35,7 @@ namespace {
 constexpr int BM = 128, BN = 128, BK = 64;
 constexpr int THREADS = 192;
 constexpr int TILE_BYTES = BM * BK * 2;  // 16 KiB, also BN * BK * 2
+constexpr int kTmemCols = 2 * BN;        // two FP32 accumulators of BN columns
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -196,7 +197,7 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
-                 "r"(BN));
+                 "r"(kTmemCols));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -239,7 +240,12 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     // ----------------------------------------------------------------- MMA
     if (lane == 0) {
       const uint32_t idesc = instr_desc(p.a_mn);
-      uint32_t accum = 0;
+      // Two accumulators: the leading product A_0 B_0 in columns [0, BN) and
+      // the small correction products (about 2^-8 of it) in [BN, 2 BN).
+      // Adding the corrections to a separate, small running sum keeps the
+      // rounding of the large sum to one addition per K term, as in an FP32
+      // GEMM, instead of six.
+      uint32_t accum[2] = {0u, 0u};
       for (int ks = 0; ks < ksteps; ++ks) {
         const int s = ks % p.stages;
         if (!mbar_wait(&full[s], (uint32_t)((ks / p.stages) & 1), p.err, 13)) break;
@@ -254,8 +260,9 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
             if (p.a_mn) ad = smem_desc(a_addr + kk * 2048, TILE_BYTES / 2, 1024);
             else        ad = smem_desc(a_addr + kk * 32, 16, 1024);
             bd = smem_desc(b_addr + kk * 32, 16, 1024);
-            mma_bf16(tmem, ad, bd, idesc, accum);
-            accum = 1;
+            const int slot = (q == 0) ? 0 : 1;
+            mma_bf16(tmem + (uint32_t)(slot * BN), ad, bd, idesc, accum[slot]);
+            accum[slot] = 1;
           }
         }
         mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
@@ -273,6 +280,12 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
       for (int c = 0; c < BN; c += 32) {
         float v[32];
         tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+        if (p.npairs > 1) {
+          float lo[32];
+          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(BN + c), lo);
+#pragma unroll
+          for (int i = 0; i < 32; ++i) v[i] += lo[i];
+        }
         if (row < p.M) {
           if (p.mode == 0) {
 #pragma unroll
@@ -314,7 +327,8 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
   if (warp == 0) {
     mbar_wait(mma_done, 0, p.err, 15);
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(BN));
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                 "r"(kTmemCols));
   }
 }
 
