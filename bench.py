@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--cpu-steps", type=int, default=1,
                     help="block steps of the oracle in the CPU-baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true",
+                    help="skip the mixed-precision lines (16384^2 and 32768x8192, b=256, q=2)")
+    ap.add_argument("--mixed-steps", type=int, default=3)
     return ap.parse_args()
 
 
@@ -283,6 +286,112 @@ def run_ours(args, world, rank, local):
     return out, A_host
 
 
+# ------------------------------------------------------- mixed precision
+
+def smooth_input_gpu(m, n, seed):
+    """A = Q1 diag(10^(-8 j/p)) Q2^T in FP32 (input preparation: the Haar
+    factors come from the library QR of seeded Gaussians on the device)."""
+    p = min(m, n)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(seed)
+    Q1 = torch.linalg.qr(torch.randn(m, p, generator=g, device="cuda"))[0]
+    Q2 = torch.linalg.qr(torch.randn(n, p, generator=g, device="cuda"))[0]
+    sig = inputs.spectrum("smooth", p).to(device="cuda", dtype=torch.float32)
+    A = (Q1 * sig) @ Q2.T
+    del Q1, Q2
+    return A, sig
+
+
+def run_mixed(args, m, n, b, q, steps, warmup, fp64_ms=None):
+    import paper_2002_06960_gb300 as pkg
+
+    A0, sig = smooth_input_gpu(m, n, args.seed)
+    A = pkg.colmajor_empty(m, n, device="cuda", dtype=torch.float32)
+    A.copy_(A0)
+    del A0
+    U = pkg.colmajor_empty(m, m, dtype=torch.float32)
+    T = pkg.colmajor_empty(m, n, dtype=torch.float32)
+    V = pkg.colmajor_empty(n, n, dtype=torch.float32)
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+
+    def step():
+        with torch.cuda.stream(stream):
+            pkg.randutv_factor_mixed(A, b, q, 0, U=U, T=T, V=V)
+
+    for _ in range(warmup):
+        step()
+    with torch.cuda.stream(stream):
+        st = pkg.randutv_stream_status()
+    if st != 0:
+        raise RuntimeError(f"mixed warm-up failed with status {st}")
+    pkg.randutv_profile_enable(True)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    prof = pkg.randutv_profile_read()
+    pkg.randutv_profile_enable(False)
+    with torch.cuda.stream(stream):
+        st = pkg.randutv_stream_status()
+    if st != 0:
+        raise RuntimeError(f"mixed step failed with status {st}")
+    flops = inputs.algorithmic_flops(m, n, b, q)
+    # errors in FP64 against the FP32 input (sampled rows / columns)
+    g = torch.Generator().manual_seed(0)
+    rows = torch.randperm(m, generator=g)[:64].cuda()
+    Ad, Ud, Td, Vd = A.double(), U.double(), T.double(), V.double()
+    rec = (Ud[rows, :] @ Td) @ Vd.T
+    recon = float(torch.linalg.norm(rec - Ad[rows, :]) / torch.linalg.norm(Ad[rows, :]))
+
+    def orth(Q):
+        k = Q.shape[1]
+        cols = torch.randperm(k, generator=g)[:64].cuda()
+        eye = torch.zeros(k, 64, dtype=torch.float64, device="cuda")
+        eye[cols, torch.arange(64, device="cuda")] = 1.0
+        return float(torch.linalg.norm(Q.T @ Q[:, cols] - eye) / 8.0)
+
+    ou, ov = orth(Ud), orth(Vd)
+    d = torch.diagonal(Td).abs()
+    p = min(m, n)
+    res = sig.double() > 1e-3
+    track = ((d[:p] / sig.double()) - 1.0).abs()
+    del Ad, Ud, Td, Vd, rec
+    bg = prof.get("bgemm_tcgen05", {"ms": 0.0, "flops": 0.0})
+    total_ms = sum(v["ms"] for v in prof.values())
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    bf16_peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    ach = bg["flops"] / (bg["ms"] * 1e-3) / 1e12 if bg["ms"] > 0 else 0.0
+    out = {
+        "workload": f"randutv_mixed_m{m}_n{n}_b{b}_q{q}",
+        "value": round(flops / (ms * 1e-3) / 1e12, 3), "unit": "TFLOP/s",
+        "ms_per_step": round(ms, 1), "steps": steps, "warmup": warmup,
+        "dtype": "bf16 sketch + bf16x3 (fp32-accurate) WY updates, fp64 Householder/SVD; fp32 I/O",
+        "input": "Q1 diag(10^(-8 j/p)) Q2^T, FP32",
+        "errors": {"recon_sampled_rows": recon, "orth_u_sampled": ou, "orth_v_sampled": ov,
+                   "sigma_track_max_rel_above_1e-3": float(track[res].max()),
+                   "sigma_track_median_rel_above_1e-3": float(track[res].median())},
+        "kernel_shares": {k: round(v["ms"] / total_ms, 4) for k, v in prof.items()
+                          if total_ms > 0 and v["launches"]},
+        "roofline": {"bound": "tensor", "kernel": "bgemm_tcgen05 (kind::f16, BF16 MMA flops)",
+                     "achieved": round(ach, 2), "peak": bf16_peak, "unit": "TFLOP/s",
+                     "frac": round(ach / bf16_peak, 4),
+                     "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"},
+    }
+    if fp64_ms:
+        fl64 = inputs.algorithmic_flops(m, n, 128, 1)
+        out["speedup_vs_fp64_path_same_n"] = round((fp64_ms / fl64) / (ms / flops), 2)
+    del A, U, T, V
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------- oracle (CPU)
 
 def oracle_sample(n, b, q, seed, steps, A=None):
@@ -340,6 +449,14 @@ def main():
             print(json.dumps(out), flush=True)
         return
     out, A_host = run_ours(args, world, rank, local)
+    if not args.no_mixed and args.n >= 1024:
+        try:
+            out["mixed"] = [run_mixed(args, args.n, args.n, 256, 2, args.mixed_steps, 3,
+                                      fp64_ms=out["ms_per_step"])]
+            if args.n == 16384:
+                out["mixed"].append(run_mixed(args, 32768, 8192, 256, 2, 1, 3))
+        except Exception as e:  # report, never hide
+            out["mixed"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = oracle_sample(args.n, args.b, args.q, args.seed,

@@ -59,9 +59,13 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
     if (!grid_barrier(a.bar, nb, a.err, 1)) return;
 
     // ---- phase 2: reflector scalars (every CTA, same order), partial dots
-    if (threadIdx.x == 0) {
+    if (warp == 0) {
+      // lanes load the partials in parallel; the fixed shuffle tree makes the
+      // sum identical in every CTA
       double sig2 = 0.0;
-      for (unsigned t = 0; t < nb; ++t) sig2 += __ldcg(a.part1 + t);
+      for (unsigned t = lane; t < nb; t += 32) sig2 += __ldcg(a.part1 + t);
+      for (int o = 16; o > 0; o >>= 1) sig2 += __shfl_xor_sync(0xffffffffu, sig2, o);
+      if (lane == 0) {
       const double alpha = __ldcg(a.A + j + j * a.lda);  // row j may be another CTA's
       double tau, scale, beta;
       if (sig2 == 0.0) {
@@ -73,36 +77,58 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
         scale = 1.0 / (alpha - beta);
       }
       s_coef[0] = tau; s_coef[1] = scale; s_coef[2] = beta;
+      }
     }
     __syncthreads();
     const double tau = s_coef[0], scale = s_coef[1];
     // dot_l = sum_{i >= j} v_i A(i, l) for l > j, v_j = 1, v_i = A(i,j) * scale
-    for (int64_t l = j + 1 + warp; l < a.c; l += nwarp) {
-      double d = 0.0;
-      const int64_t lo = (i0 > j) ? i0 : j;
+    // Each warp takes its columns l = j+1+warp+nwarp*t in groups of 8 and
+    // walks its rows once per group, so the loads of a row are independent
+    // and in flight together.
+    const int64_t lo = (i0 > j) ? i0 : j;
+    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)nwarp) {
+      double d[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) d[t] = 0.0;
       for (int64_t i = lo + lane; i < i1; i += 32) {
         const double v = (i == j) ? 1.0 : a.A[i + j * a.lda] * scale;
-        d = fma(v, a.A[i + l * a.lda], d);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int64_t l = l0 + (int64_t)t * nwarp;
+          if (l < a.c) d[t] = fma(v, a.A[i + l * a.lda], d[t]);
+        }
       }
-      for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
-      if (lane == 0) a.part2[(int64_t)blockIdx.x * a.c + l] = d;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        double x = d[t];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        const int64_t l = l0 + (int64_t)t * nwarp;
+        if (lane == 0 && l < a.c) a.part2[(int64_t)blockIdx.x * a.c + l] = x;
+      }
     }
     if (!grid_barrier(a.bar, nb, a.err, 2)) return;
 
     // ---- phase 3: rank-1 update of own rows, write W(:, j), R(j, j), zeros
     // w_l = tau * sum_t part2[t][l]  (each warp sums the columns it updates)
-    for (int64_t l = j + 1 + warp; l < a.c; l += nwarp) {
-      double wl = 0.0;
-      if (lane == 0) {
-        for (unsigned t = 0; t < nb; ++t) wl += __ldcg(a.part2 + (int64_t)t * a.c + l);
-        wl *= tau;
+    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)nwarp) {
+      double w[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        const int64_t l = l0 + (int64_t)t * nwarp;
+        double s = 0.0;
+        if (l < a.c)
+          for (unsigned u = lane; u < nb; u += 32) s += __ldcg(a.part2 + (int64_t)u * a.c + l);
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        w[t] = s * tau;
       }
-      wl = __shfl_sync(0xffffffffu, wl, 0);
       if (tau != 0.0) {
-        const int64_t lo = (i0 > j) ? i0 : j;
         for (int64_t i = lo + lane; i < i1; i += 32) {
           const double v = (i == j) ? 1.0 : a.A[i + j * a.lda] * scale;
-          a.A[i + l * a.lda] = fma(-v, wl, a.A[i + l * a.lda]);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int64_t l = l0 + (int64_t)t * nwarp;
+            if (l < a.c) a.A[i + l * a.lda] = fma(-v, w[t], a.A[i + l * a.lda]);
+          }
         }
       }
     }

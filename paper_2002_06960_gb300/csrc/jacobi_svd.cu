@@ -2,17 +2,18 @@
 // §3.1 step 3), one-sided Jacobi in FP64 (Hestenes 1958; Demmel & Veselic
 // 1992 for the rotation and the stopping rule).
 //
-// Layout: one thread-block cluster of 8 CTAs.  CTA k holds rows
-// [k R, (k+1) R) of both the working matrix B (which converges to U diag(D))
-// and the accumulated rotation V, R = ceil(b/8), in shared memory.  A sweep
-// is b-1 rounds of the round-robin (circle) ordering, each round rotating b/2
-// disjoint column pairs.  Per round every CTA writes the partial inner
-// products (|a_p|^2, |a_q|^2, a_p.a_q) of its rows, a cluster barrier
-// follows, and every CTA sums the 8 partials of each pair in CTA order
-// through distributed shared memory.  The rotation parameters are therefore
-// bitwise identical in all CTAs, which apply them to their own rows, and all
-// CTAs take the same convergence decision.  FP64 throughput per SM is low on
-// this part, which is why the rows are spread over 8 SMs.
+// Layout: one thread-block cluster of C CTAs (16 where the device can place
+// that non-portable size, else 8).  CTA k holds rows [k R, (k+1) R) of both
+// the working matrix B (which converges to U diag(D)) and the accumulated
+// rotation V, R = ceil(b/C), in shared memory.  A sweep is b-1 rounds of the
+// round-robin (circle) ordering, each round rotating b/2 disjoint column
+// pairs.  Per round every CTA writes the partial inner products
+// (|a_p|^2, |a_q|^2, a_p.a_q) of its rows, a cluster barrier follows, and
+// every CTA combines the C partials of each pair in a fixed order through
+// distributed shared memory.  The rotation parameters are therefore bitwise
+// identical in all CTAs, which apply them to their own rows, and all CTAs
+// take the same convergence decision.  FP64 throughput per SM is low on this
+// part (two DFMA per clock), which is why the rows are spread over C SMs.
 //
 // After convergence: D_j = |b_j|, columns sorted by descending D (lowest
 // index first on ties), U_j = b_j / D_j, and each column of V signed so that
@@ -58,7 +59,7 @@ __device__ __forceinline__ void rr_pair(int round, int t, int P, int* p, int* q)
   *q = a < c ? c : a;
 }
 
-__global__ void __cluster_dims__(SVD_CL, 1, 1) __launch_bounds__(SVD_THREADS)
+__global__ void __launch_bounds__(SVD_THREADS)
 jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __restrict__ D,
                   double* __restrict__ Us, double* __restrict__ Vs, int max_sweeps,
                   unsigned* __restrict__ info) {
@@ -68,7 +69,8 @@ jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __r
   L.b = b;
   L.P = (b + 1) & ~1;
   L.npairs = L.P / 2;
-  L.R = (b + SVD_CL - 1) / SVD_CL;
+  const int ncl = (int)cl.num_blocks();  // 16 where the device allows it, else 8
+  L.R = (b + ncl - 1) / ncl;
   L.LDR = L.R + 1;
   const int P = L.P, npairs = L.npairs, R = L.R, LDR = L.LDR;
   const int r0 = rank * R;
@@ -138,29 +140,33 @@ jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __r
       }
       cl.sync();
       // cluster sums in CTA order, rotation parameters
+      // The threads of the group load the 8 CTAs' partials in parallel and
+      // combine them with a fixed shuffle tree: every thread (of every CTA)
+      // ends with the same sums and takes the same rotation.
       double c = 1.0, s = 0.0;
       int rot = 0;
-      if (active && sub == 0) {
+      {
         double al = 0.0, be = 0.0, ga = 0.0;
-        for (int k = 0; k < SVD_CL; ++k) {
-          const double* rp = cl.map_shared_rank(part, k) + ((size_t)buf * npairs + g) * 3;
-          al += rp[0];
-          be += rp[1];
-          ga += rp[2];
+        if (active) {
+          for (int k = sub; k < ncl; k += tpp) {
+            const double* rp = cl.map_shared_rank(part, k) + ((size_t)buf * npairs + g) * 3;
+            al += rp[0];
+            be += rp[1];
+            ga += rp[2];
+          }
         }
-        if (q < b && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+        for (int o = tpp >> 1; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
+        }
+        if (active && q < b && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
           const double zeta = (be - al) / (2.0 * ga);
           const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
           c = 1.0 / sqrt(fma(t, t, 1.0));
           s = c * t;
           rot = 1;
         }
-      }
-      if (tpp > 1) {
-        const int lead = (threadIdx.x & 31) & ~(tpp - 1);
-        c = __shfl_sync(0xffffffffu, c, lead);
-        s = __shfl_sync(0xffffffffu, s, lead);
-        rot = __shfl_sync(0xffffffffu, rot, lead);
       }
       if (active && rot) {
         if (sub == 0) s_rotated = 1;
@@ -211,7 +217,7 @@ jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __r
     // signed value is fetched from the owning CTA once the winner is known.
     double s2 = 0.0, bestabs = -1.0;
     int bestk = 0;
-    for (int k = 0; k < SVD_CL; ++k) {
+    for (int k = 0; k < ncl; ++k) {
       s2 += cl.map_shared_rank(npart, k)[j];
       const double a = fabs(cl.map_shared_rank(vmax, k)[j]);
       if (a > bestabs) {  // strict: lower rows (CTAs) win ties
@@ -294,18 +300,58 @@ int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us,
   L.b = b;
   L.P = (b + 1) & ~1;
   L.npairs = L.P / 2;
-  L.R = (b + SVD_CL - 1) / SVD_CL;
+  // A cluster of 16 CTAs (a non-portable size) halves each CTA's FP64 work
+  // per round; fall back to the portable 8 where the device cannot place 16.
+  static int ncl = 0;
+  static size_t configured = 0;
+  if (ncl == 0) {
+    RUTV_CK(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
+                                 1));
+    RUTV_CK(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 160 * 1024));
+    configured = 160 * 1024;
+    cudaLaunchConfig_t cfg = {};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 16;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(16);
+    cfg.blockDim = dim3(SVD_THREADS);
+    cfg.dynamicSmemBytes = 100 * 1024;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)jacobi_svd_kernel, &cfg) == cudaSuccess &&
+        nclusters > 0)
+      ncl = 16;
+    else
+      ncl = SVD_CL;
+    cudaGetLastError();
+  }
+  L.R = (b + ncl - 1) / ncl;
   L.LDR = L.R + 1;
   const size_t smem = L.bytes();
-  static size_t configured = 0;
-  if (smem > 48 * 1024 && smem > configured) {
+  if (smem > configured) {
     RUTV_CK(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     configured = smem;
   }
   ProfScope prof(K_SVD, 0.0, 32.0 * (double)b * b, st);
   const int max_sweeps = 40;
-  jacobi_svd_kernel<<<SVD_CL, SVD_THREADS, smem, st>>>(b, B, ldb, D, Us, Vs, max_sweeps, info);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ncl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)ncl);
+  cfg.blockDim = dim3(SVD_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  RUTV_CK(cudaLaunchKernelEx(&cfg, jacobi_svd_kernel, b, B, ldb, D, Us, Vs, max_sweeps, info));
   note_launch();
   RUTV_CK(cudaGetLastError());
   complete_basis_kernel<<<1, SVD_THREADS, 0, st>>>(b, D, Us);
