@@ -82,13 +82,14 @@ def householder_qr(Y: torch.Tensor):
     W = torch.zeros(r, c, dtype=A.dtype)
     tau = torch.zeros(c, dtype=A.dtype)
     for j in range(c):
-        v, t, beta = householder_reflector(A[j:, j])
+        v, t, beta = householder_reflector(A[j:, j].clone())
         W[j:, j] = v
         tau[j] = t
         # apply H_j to the trailing columns
         if j + 1 < c:
-            w = t * (v @ A[j:, j + 1:])
-            A[j:, j + 1:] = A[j:, j + 1:] - torch.outer(v, w)
+            X = A[j:, j + 1:].clone()
+            w = t * (v @ X)
+            A[j:, j + 1:] = X - torch.outer(v, w)
         A[j, j] = beta
         A[j + 1:, j] = 0.0
     R = torch.triu(A[:c, :])
@@ -103,7 +104,7 @@ def wy_factor(W: torch.Tensor, tau: torch.Tensor) -> torch.Tensor:
         S[j, j] = tau[j]
         if j > 0:
             z = W[:, :j].T @ W[:, j]
-            S[:j, j] = -tau[j] * (S[:j, :j] @ z)
+            S[:j, j] = -tau[j] * (S[:j, :j].clone() @ z)
     return S
 
 
@@ -173,11 +174,14 @@ def range_basis(T22: torch.Tensor, G: torch.Tensor, q: int) -> torch.Tensor:
 
 def randutv(A: torch.Tensor, b: int, q: int, seed: int, want_u: bool = True,
             want_v: bool = True, matrix_id: int = 0, max_steps: int | None = None,
-            state: Factorization | None = None) -> Factorization:
+            state: Factorization | None = None, svd: bool = True) -> Factorization:
     """A = U T V^T by blocked randUTV.
 
     ``max_steps`` stops after that many steps (a partial factorization);
-    ``state`` resumes from the result of an earlier call.
+    ``state`` resumes from the result of an earlier call.  ``svd=False``
+    leaves out the small SVDs (T is then block upper triangular); the spans
+    of U(:, 0:k) and V(:, 0:k) at every block boundary k, and the trailing
+    matrices of later steps, do not depend on them.
     """
     A = A.to(f64)
     m, n = A.shape
@@ -200,24 +204,34 @@ def randutv(A: torch.Tensor, b: int, q: int, seed: int, want_u: bool = True,
         if max_steps is not None and i >= max_steps:
             break
         # -- right transform: V-hat from the sketch (§3.1 step 1; Fig. 2) --
+        # (the operands are copied out before each update is written back, so
+        # that the function can also be differentiated by torch autograd)
         if right:
             G = sketch(seed, i, rm, bi, matrix_id)
-            Y = range_basis(T[k:, k:], G, q)
+            Y = range_basis(T[k:, k:].clone(), G, q)
             W, tau, _ = householder_qr(Y)
             S = wy_factor(W, tau)
-            T[:, k:] = T[:, k:] - (T[:, k:] @ W) @ S @ W.T
+            X = T[:, k:].clone()
+            T[:, k:] = X - (X @ W) @ S @ W.T
             if V is not None:
-                V[:, k:] = V[:, k:] - (V[:, k:] @ W) @ S @ W.T
+                X = V[:, k:].clone()
+                V[:, k:] = X - (X @ W) @ S @ W.T
         # -- left transform: QR of the new column panel (§3.1 step 2; Fig. 2) --
         if left:
-            W, tau, R = householder_qr(T[k:, k:k + bi])
+            W, tau, R = householder_qr(T[k:, k:k + bi].clone())
             S = wy_factor(W, tau)
             T[k:, k:k + bi] = 0.0
             T[k:k + bi, k:k + bi] = R
-            T[k:, k + bi:] = T[k:, k + bi:] - W @ (S.T @ (W.T @ T[k:, k + bi:]))
+            X = T[k:, k + bi:].clone()
+            T[k:, k + bi:] = X - W @ (S.T @ (W.T @ X))
             if U is not None:
-                U[:, k:] = U[:, k:] - (U[:, k:] @ W) @ S @ W.T
+                X = U[:, k:].clone()
+                U[:, k:] = X - (X @ W) @ S @ W.T
         # -- small SVD of the diagonal block and its fold-back (§3.1 steps 3-6) --
+        if not svd:
+            steps = i + 1
+            last_k = k + bi
+            continue
         Us, D, Vs = small_svd(T[k:k + bi, k:k + bi])
         T[k:k + bi, k:k + bi] = torch.diag(D)
         T[:k, k:k + bi] = T[:k, k:k + bi] @ Vs
@@ -234,10 +248,17 @@ def randutv(A: torch.Tensor, b: int, q: int, seed: int, want_u: bool = True,
 def lowrank(A: torch.Tensor, k: int, b: int, q: int, seed: int) -> torch.Tensor:
     """A_k = U(:, 0:k) U(:, 0:k)^T A (§1.1: A_k = U(:,1:k) R(1:k,:) V^*).
 
-    Only the ceil(k/b) steps that fix the first k columns of U are run.
+    k is a multiple of b.  Only the k/b steps that fix the span of the first
+    k columns of U are run, and without the small SVDs: they rotate columns
+    inside a block and change neither that span nor the trailing matrix of
+    any later step, so A_k is the same and is differentiable through the
+    Householder steps alone (torch autograd of this function is the FP64
+    reference gradient).
     """
-    steps = -(-k // b)
-    f = randutv(A, b, q, seed, want_u=True, want_v=False, max_steps=steps)
+    if k % b != 0:
+        raise ValueError("k must be a multiple of b")
+    steps = k // b
+    f = randutv(A, b, q, seed, want_u=True, want_v=False, max_steps=steps, svd=False)
     Uk = f.U[:, :k]
     return Uk @ (Uk.T @ A.to(f64))
 

@@ -424,3 +424,60 @@ def test_first_block_of_v_spans_the_sketched_range(q):
     for q2 in {0, 1, 2} - {q}:
         Y2 = (Q2 * sig ** (2 * q2 + 1)) @ (Q1.T @ G0)
         assert float((Y2 - Vb @ (Vb.T @ Y2)).norm()) > 1e-6 * float(Y2.norm())
+
+
+# ------------------------------------------------- gradient of the low-rank map
+
+def _loss(A, B, k, b, q, seed):
+    Ak = oracle.lowrank(A, k, b, q, seed)
+    return ((Ak - B) ** 2).sum()
+
+
+def _grad(A, B, k, b, q, seed):
+    X = A.clone().requires_grad_(True)
+    L = _loss(X, B, k, b, q, seed)
+    (g,) = torch.autograd.grad(L, X)
+    return g
+
+
+@pytest.mark.parametrize("m,n,b,k,q", [(40, 36, 8, 16, 1), (30, 44, 6, 12, 2), (24, 24, 8, 8, 0)])
+def test_lowrank_gradient_central_differences(m, n, b, k, q):
+    """Autograd through the oracle matches FP64 central differences."""
+    A = inputs.matrix("exp16", m, n, seed=3)
+    B = inputs.gaussian(m, n, seed=4, stream=inputs.STREAM_B)
+    g = _grad(A, B, k, b, q, 7)
+    gen = torch.Generator().manual_seed(11)
+    h = 1e-6 * float(A.norm())
+    for _ in range(3):
+        E = torch.randn(m, n, generator=gen, dtype=f64)
+        E /= E.norm()
+        fd = (float(_loss(A + h * E, B, k, b, q, 7)) - float(_loss(A - h * E, B, k, b, q, 7))) / (2 * h)
+        an = float((g * E).sum())
+        assert abs(an - fd) <= 1e-6 * max(1.0, abs(fd)), (an, fd)
+
+
+def test_lowrank_gradient_128_step_spectrum():
+    """The 128 x 128 check instance: b = 16, k = 32, q = 1, step spectrum with the gap at 32."""
+    n, b, k, q = 128, 16, 32, 1
+    A = inputs.matrix("step", n, n, seed=3, gap=k)
+    B = inputs.gaussian(n, n, seed=3, stream=inputs.STREAM_B)
+    g = _grad(A, B, k, b, q, 0)
+    gen = torch.Generator().manual_seed(5)
+    h = 1e-6 * float(A.norm())
+    for _ in range(3):
+        E = torch.randn(n, n, generator=gen, dtype=f64)
+        E /= E.norm()
+        fd = (float(_loss(A + h * E, B, k, b, q, 0)) - float(_loss(A - h * E, B, k, b, q, 0))) / (2 * h)
+        an = float((g * E).sum())
+        assert abs(an - fd) <= 1e-6 * max(1.0, abs(fd)), (an, fd)
+
+
+def test_lowrank_without_svd_is_unchanged():
+    A = inputs.gaussian(50, 40, seed=2)
+    full = oracle.randutv(A, 8, 1, seed=3, max_steps=2)
+    nosvd = oracle.randutv(A, 8, 1, seed=3, max_steps=2, svd=False)
+    P1 = full.U[:, :16] @ full.U[:, :16].T
+    P2 = nosvd.U[:, :16] @ nosvd.U[:, :16].T
+    assert torch.allclose(P1, P2, atol=1e-13)
+    # the trailing matrix after the steps is the same too
+    assert torch.allclose(full.T[16:, 16:], nosvd.T[16:, 16:], atol=1e-13)
