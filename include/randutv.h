@@ -107,6 +107,63 @@ int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int 
                          uint64_t seed, float* U, float* T, float* V, int max_steps,
                          void* stream);
 
+/* ----------------------------------------------------------------- batched --
+ * Many FP32 matrices of uneven sizes (1 <= m, n <= 1024), each factored by the
+ * block steps of §3.1 / Fig. 2, in ONE persistent launch: each CTA takes the
+ * next matrix from a device queue ordered by descending cost.  Arithmetic:
+ * FP32 storage and FFMA products; Householder norms and scalars in FP64;
+ * FP32 one-sided Jacobi for the b x b SVD; the sketch uses the Philox words
+ * of randutv_philox_normal with counter (pair, step, matrix index, 0) and a
+ * single-precision Box-Muller (u1 = ((x0 >> 8) + 1) 2^-24, u2 = (x2 >> 8) 2^-24).
+ *   batch (2)        number of matrices.
+ *   m, n, lda (3,4,7) HOST arrays of length batch.
+ *   A (5)            HOST array of DEVICE pointers, matrix i is m[i] x n[i].
+ *   b (8)            16, 32 or 64 for every matrix, or 0 for the tuned
+ *                    per-size table (randutv_batched_set_tuning; default 32).
+ *   q (9), seed (10) as in randutv_factor.
+ *   U, T, V (11-13)  HOST arrays of DEVICE pointers (ld m[i], m[i], n[i]);
+ *                    U or V may be NULL (no factors for any matrix).
+ * The plan uploads the descriptors (synchronously) and owns the queue and
+ * the per-CTA workspace; randutv_batched_run is one memset and one kernel
+ * launch on `stream`, so it can be captured in a CUDA graph and replayed
+ * (each replay refactors the same matrices).  info (device, batch ints)
+ * receives 0 or RANDUTV_ENONFINITE per matrix. */
+int randutv_batched_plan_create(void** plan, int batch, const int64_t* m, const int64_t* n,
+                                const float* const* A, const int64_t* lda, int b, int q,
+                                uint64_t seed, float* const* U, float* const* T,
+                                float* const* V);
+int randutv_batched_run(void* plan, int* info, void* stream);
+int randutv_batched_plan_destroy(void* plan);
+
+/* One-shot form: plan, run on `stream`, wait, destroy. */
+int randutv_factor_batched(int batch, const int64_t* m, const int64_t* n, const float* const* A,
+                           const int64_t* lda, int b, int q, uint64_t seed, float* const* U,
+                           float* const* T, float* const* V, int* info, void* stream);
+
+/* Autotuner output: block size (16, 32, 64, or 0 = default 32) for each of
+ * `nclasses` <= 8 size classes, class c holding max(m, n) in (128c, 128(c+1)],
+ * and CTAs per SM for the persistent grid (0 = occupancy limit). */
+int randutv_batched_set_tuning(const int* b_for_class, int nclasses, int ctas_per_sm);
+
+/* ---------------------------------------------------- low rank and adjoint --
+ * A_k = U(:, 0:k) U(:, 0:k)^T A, the rank-k approximation of §1.1
+ * (A_k = U(:,1:k) R(1:k,:) V^*), through the first k/b block steps of §3.1
+ * with the sketch fixed by `seed`.  FP64; all pointers DEVICE.
+ *   m, n (1, 2); A (3) m x n with lda (4) >= m, read only;
+ *   k (5): 1 <= k < min(m, n); b (6): 1 <= b <= 256 and b divides k;
+ *   q (7), seed (8) as in randutv_factor.
+ * The block SVDs rotate columns inside a block and leave the span of
+ * U(:, 0:k) unchanged, so they are not computed.  Synchronous. */
+int randutv_lowrank(int64_t m, int64_t n, const double* A, int64_t lda, int k, int b, int q,
+                    uint64_t seed, double* Ak /* (9) m x n, ld m */, void* stream);
+
+/* Adjoint (vector-Jacobian product) of randutv_lowrank in A, the sketch held
+ * fixed: dA (10, m x n, ld m) = (d A_k / d A)^T dAk (9, m x n, ld m).  The
+ * per-step Householder factors are recomputed from A and the seed (nothing
+ * is kept from the forward call).  Synchronous; same argument rules. */
+int randutv_lowrank_backward(int64_t m, int64_t n, const double* A, int64_t lda, int k, int b,
+                             int q, uint64_t seed, const double* dAk, double* dA, void* stream);
+
 /* Tensor-core GEMM of the mixed path, FP32 in and out:
  * C = alpha op(A) B + beta C with op(A) = A (transa 'N', A is M x K, MN-major
  * operand) or A^T (transa 'T', A is K x M, K-major operand), B K x N.  The

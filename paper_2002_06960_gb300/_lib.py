@@ -49,6 +49,16 @@ _SIGS = {
     "randutv_gemm_bf16": (c_int, [ctypes.c_char, c_i64, c_i64, c_i64, ctypes.c_float, c_vp, c_i64,
                                   c_vp, c_i64, ctypes.c_float, c_vp, c_i64, c_int, c_vp]),
     "randutv_householder_qr_noalloc": (c_int, [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
+    "randutv_batched_plan_create": (c_int, [ctypes.POINTER(c_vp), c_int, c_vp, c_vp, c_vp, c_vp,
+                                            c_int, c_int, c_u64, c_vp, c_vp, c_vp]),
+    "randutv_batched_run": (c_int, [c_vp, c_vp, c_vp]),
+    "randutv_batched_plan_destroy": (c_int, [c_vp]),
+    "randutv_factor_batched": (c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_u64, c_vp,
+                                       c_vp, c_vp, c_vp, c_vp]),
+    "randutv_batched_set_tuning": (c_int, [c_vp, c_int, c_int]),
+    "randutv_lowrank": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64, c_vp, c_vp]),
+    "randutv_lowrank_backward": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64,
+                                         c_vp, c_vp, c_vp]),
     "randutv_profile_enable": (None, [c_int]),
     "randutv_profile_read": (c_int, [c_vp, c_int]),
     "randutv_profile_class_name": (ctypes.c_char_p, [c_int]),

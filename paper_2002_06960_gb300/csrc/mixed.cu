@@ -30,6 +30,12 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ src, int64_t lds, in
   }
 }
 
+// tau_j <- 2 / Gm(j, j) for the reflectors that are not the identity (tau_j = 0).
+__global__ void retau_kernel(int c, const double* __restrict__ Gm, double* __restrict__ tau) {
+  for (int j = threadIdx.x; j < c; j += blockDim.x)
+    if (tau[j] != 0.0) tau[j] = 2.0 / Gm[j + (int64_t)j * c];
+}
+
 int grid_of(int64_t total) {
   int64_t blocks = (total + 255) / 256;
   const int64_t cap = (int64_t)dev_info().sms * 16;
@@ -98,7 +104,7 @@ struct MixedWork {
   Planes T, Ut, Vt;             // m x n, m x m (U^T), n x n (V^T)
   Planes W, WSt, Xp, Sp, Us, Vs; // small operands as planes
   __nv_bfloat16 *G, *Yb;        // BF16 sketch operands
-  float *Y, *Z, *X, *tmp, *Gram32, *scal;
+  float *Y, *Z, *X, *tmp, *scal;
   double *Y64, *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64, *WS64;
   char* qr;
   double* dgemm;
@@ -135,7 +141,6 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add((size_t)pad8(big) * b * 2); // G
   add((size_t)pad8(big) * b * 2); // Yb
   for (int i = 0; i < 4; ++i) add((size_t)big * b * 4);  // Y, Z, X, tmp
-  add((size_t)b * b * 4 + 256);   // Gram32
   add(256);                       // scal
   for (int i = 0; i < 3; ++i) add((size_t)big * b * 8);  // Y64, W64, WS64
   add((size_t)b * 8 * 2);         // tau, D
@@ -163,7 +168,6 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.Z = (float*)ar.take((size_t)big * b * 4);
   w.X = (float*)ar.take((size_t)big * b * 4);
   w.tmp = (float*)ar.take((size_t)big * b * 4);
-  w.Gram32 = (float*)ar.take((size_t)b * b * 4 + 256);
   w.scal = (float*)ar.take(256);
   w.Y64 = (double*)ar.take((size_t)big * b * 8);
   w.W64 = (double*)ar.take((size_t)big * b * 8);
@@ -193,13 +197,21 @@ struct MCtx {
 
 // From the FP64 reflectors W64 (r x bi) and tau: W planes, S (FP64), and
 // WSt = (W S^T)^T as planes (bi x r).
+//
+// The reflectors the updates apply are the rounded W~ held in the planes.  S
+// is built from W~ itself: its Gram W~^T W~ in FP64 (over r terms; an FP32
+// accumulation would be off by about sqrt(r) ulp) and tau~_j = 2 / |w~_j|^2,
+// so that every H_j = I - tau~_j w~_j w~_j^T, and with them I - W~ S W~^T,
+// is orthogonal to FP64 accuracy rather than to the accuracy of the rounding.
 int mixed_wy(MCtx& c, int64_t r, int64_t bi) {
   MixedWork& w = c.w;
   RUTV_TRY(split_f64(w.W64, r, r, bi, 0, w.W, 0, 0, c.st));
-  // Gram = W^T W to FP32 accuracy, then S in FP64
-  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, bi), opnd(w.W, 3, 0, 0, 0, r, bi), (int)bi, (int)bi, (int)r, 3,
-                        out_f32(w.Gram32, bi), c.status, c.st));
-  RUTV_TRY(f32_to_f64(w.Gram32, bi, bi, bi, w.Gram64, bi, c.st));
+  RUTV_TRY(merge_f64(w.W, 0, 0, r, bi, 0, w.W64, r, c.st));
+  RUTV_TRY(launch_dgemm(true, false, bi, bi, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, bi, w.dgemm,
+                        w.dgemm_bytes, c.st));
+  retau_kernel<<<1, 256, 0, c.st>>>((int)bi, w.Gram64, w.tau);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
   RUTV_TRY(launch_wy_factor(bi, w.Gram64, w.tau, w.S64, c.st));
   // WS = W S^T (r x bi): A = W (MN-major), B = S^T held as planes of S^T
   RUTV_TRY(split_f64(w.S64, bi, bi, bi, 1, w.Sp, 0, 0, c.st));

@@ -7,41 +7,9 @@
 // between steps, a resumed factorization draws the same sketch, and the CPU
 // checker draws the same words.
 #include "common.cuh"
+#include "philox.cuh"
 
 namespace rutv {
-
-struct PhiloxKey {
-  uint32_t k0, k1;
-};
-
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey k) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-  for (int r = 0; r < 10; ++r) {
-    if (r > 0) {
-      k.k0 += W0;
-      k.k1 += W1;
-    }
-    const uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-    const uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-    c = make_uint4(hi1 ^ c.y ^ k.k0, lo1, hi0 ^ c.w ^ k.k1, lo0);
-  }
-  return c;
-}
-
-// Two normals from one counter: 53-bit uniforms u1 in (0,1], u2 in [0,1).
-__device__ __forceinline__ void box_muller(uint4 w, double* z0, double* z1) {
-  const uint64_t j1 = (uint64_t)(w.x >> 5) * 67108864ull + (uint64_t)(w.y >> 6);
-  const uint64_t j2 = (uint64_t)(w.z >> 5) * 67108864ull + (uint64_t)(w.w >> 6);
-  const double u1 = (double)(j1 + 1ull) * 0x1.0p-53;
-  const double u2 = (double)j2 * 0x1.0p-53;
-  const double rho = sqrt(-2.0 * log(u1));
-  double s, c;
-  sincospi(2.0 * u2, &s, &c);
-  *z0 = rho * c;
-  *z1 = rho * s;
-}
 
 __global__ void philox_normal_kernel(PhiloxKey key, uint32_t step, uint32_t mid, uint32_t sid,
                                      int64_t rows, int64_t count, double* __restrict__ G,

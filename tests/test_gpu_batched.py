@@ -1,0 +1,112 @@
+"""Batched randUTV (one persistent launch over uneven sizes) against the oracle.
+
+Each matrix of the batch is checked by its errors against the FP64 oracle
+run on the same input: reconstruction and orthogonality at the FP32 level,
+exact zeros below the diagonal, and the leading diagonal of T (the
+singular-value estimates) close to the oracle's.  The launch is also checked
+for determinism, for giving the same result when captured in a CUDA graph
+and replayed, and for per-matrix status reporting.
+"""
+import pytest
+import torch
+
+import oracle
+from paper_2002_06960_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+f32, f64 = torch.float32, torch.float64
+
+
+@pytest.fixture(scope="module")
+def pkg():
+    from paper_2002_06960_gb300 import build
+    build.build()
+    import paper_2002_06960_gb300 as p
+    p.lib()
+    from paper_2002_06960_gb300 import batched
+    return p, batched
+
+
+def _mats(p, sizes, seed=2):
+    out = []
+    for i, (m, n) in enumerate(sizes):
+        sig = torch.exp(-torch.arange(min(m, n), dtype=f64) / 16.0)
+        A = inputs.prescribed(m, n, sig, seed=seed + i) if min(m, n) > 1 else \
+            inputs.gaussian(m, n, seed=seed + i)
+        out.append((A, p.to_colmajor(A.to(f32), "cuda")))
+    return out
+
+
+SIZES = [(200, 150), (150, 200), (64, 64), (300, 97), (33, 257), (16, 16), (1, 1), (1, 7), (9, 1),
+         (128, 128), (257, 33)]
+
+
+@pytest.mark.parametrize("b", [16, 32, 64])
+def test_batched_errors_against_oracle(pkg, b):
+    p, batched = pkg
+    mats = _mats(p, SIZES)
+    plan = batched.BatchedPlan([d for _, d in mats], b=b, q=1, seed=5)
+    plan.run()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().sum()) == 0
+    for i, (A, _) in enumerate(mats):
+        U, T, V = (plan.U[i].cpu().double(), plan.T[i].cpu().double(), plan.V[i].cpu().double())
+        Aq = A.to(f32).double()
+        recon = oracle.recon_error(Aq, U, T, V)
+        assert recon < 2e-6, (i, recon)
+        assert oracle.orth_error(U) < 2e-6 and oracle.orth_error(V) < 2e-6, i
+        assert float(torch.tril(T, -1).abs().max()) == 0.0
+        ref = oracle.randutv(Aq, b, 1, 5, matrix_id=i)
+        d, d0 = torch.diagonal(T).abs(), torch.diagonal(ref.T).abs()
+        k = min(8, d.numel())
+        assert float(((d[:k] - d0[:k]).abs() / d0[:k].clamp_min(1e-30)).max()) < 1e-3, i
+    plan.close()
+
+
+def test_batched_is_deterministic_and_graph_replays(pkg):
+    p, batched = pkg
+    mats = _mats(p, SIZES[:6], seed=9)
+    plan = batched.BatchedPlan([d for _, d in mats], b=32, q=1, seed=1)
+    plan.run()
+    torch.cuda.synchronize()
+    T1 = [t.clone() for t in plan.T]
+    plan.run()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(T1, plan.T))
+    for t in plan.T:
+        t.zero_()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            plan.run()
+    g.replay()
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(T1, plan.T))
+    plan.close()
+
+
+def test_batched_reports_nonfinite_per_matrix(pkg):
+    p, batched = pkg
+    mats = _mats(p, [(40, 30), (30, 40), (50, 50)], seed=4)
+    devs = [d for _, d in mats]
+    devs[1][3, 5] = float("nan")
+    plan = batched.BatchedPlan(devs, b=16, q=1, seed=0)
+    plan.run()
+    torch.cuda.synchronize()
+    assert plan.info.tolist() == [0, 2, 0]
+    plan.close()
+
+
+def test_autotuner_installs_a_table(pkg):
+    p, batched = pkg
+
+    def make(m, n, i):
+        return p.to_colmajor(inputs.gaussian(m, n, seed=i).to(f32), "cuda")
+
+    rep = batched.autotune(make, per_class=4, reps=1, classes=[0, 1])
+    assert set(rep) == {0, 1}
+    assert all(b in (16, 32, 64) and ms > 0 for b, ms in rep.values())
+    batched.set_tuning([0] * batched.N_CLASSES)  # back to the default
