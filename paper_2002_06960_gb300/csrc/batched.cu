@@ -310,22 +310,40 @@ __device__ void cta_svd(int bi, const float* Bg, int64_t ldb, float* Us, float* 
   while (tpp < 32 && tpp * 2 * npairs <= BT) tpp *= 2;
   const int g = tid / tpp, sub = tid % tpp;
   const bool active = g < npairs;
-  const float tol = (float)(bi > 1 ? bi : 1) * 0x1.0p-24f;
+  // The stopping threshold on |cos| is a few FP32 ulps, independent of bi: the
+  // orthogonality of U_s = B V / D is that of the converged columns, and it
+  // enters U and T at every fold-back.  Reaching it needs a_p.a_q without the
+  // rounding noise of an FP32 dot product (about sqrt(bi) ulp of |a_p||a_q|,
+  // which near convergence is far above a_p.a_q itself), so that one is a
+  // compensated dot product.  Every lane of a group ends with bit-identical
+  // sums, hence every row of the pair gets the same rotation.
+  const float tol = 4.f * 0x1.0p-24f;
   for (int sweep = 0; sweep < 30; ++sweep) {
     for (int round = 0; round < P - 1; ++round) {
       int p = 0, q = 0;
       if (active) rr_pair_b(round, g, P, &p, &q);
-      float sa = 0.f, sb = 0.f, sc = 0.f;
+      float sa = 0.f, sb = 0.f, sc = 0.f, scc = 0.f;
       if (active)
         for (int i = sub; i < bi; i += tpp) {
           const float x = sm.svB[p][i], y = sm.svB[q][i];
-          sa = fmaf(x, x, sa); sb = fmaf(y, y, sb); sc = fmaf(x, y, sc);
+          sa = fmaf(x, x, sa); sb = fmaf(y, y, sb);
+          const float pr = x * y, pe = fmaf(x, y, -pr);
+          float t, te;
+          two_sum(sc, pr, t, te);
+          sc = t;
+          scc += te + pe;
         }
       for (int o = tpp >> 1; o > 0; o >>= 1) {
         sa += __shfl_xor_sync(0xffffffffu, sa, o);
         sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        const float s2 = __shfl_xor_sync(0xffffffffu, sc, o);
+        const float c2 = __shfl_xor_sync(0xffffffffu, scc, o);
+        float t, te;
+        two_sum(sc, s2, t, te);  // t and te do not depend on the operand order
+        sc = t;
+        scc = (scc + c2) + te;   // nor does this sum
       }
+      sc += scc;
       if (active && q < bi && sc != 0.f && fabsf(sc) > tol * sqrtf(sa) * sqrtf(sb)) {
         const float zeta = (sb - sa) / (2.f * sc);
         const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));

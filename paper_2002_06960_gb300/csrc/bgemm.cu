@@ -32,10 +32,11 @@ namespace rutv {
 
 namespace {
 
-constexpr int BM = 128, BN = 128, BK = 64;
+constexpr int BM = 128, BN = 64, BK = 64;
 constexpr int THREADS = 192;
-constexpr int TILE_BYTES = BM * BK * 2;  // 16 KiB, also BN * BK * 2
-constexpr int kTmemCols = 2 * BN;        // two FP32 accumulators of BN columns
+constexpr int A_TILE = BM * BK * 2;  // 16 KiB
+constexpr int B_TILE = BN * BK * 2;  // 8 KiB
+constexpr int kTmemCols = 4 * BN;    // two buffers x (leading, correction) accumulators
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -148,10 +149,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Error-free transformation of a sum: s + e == a + b exactly (Knuth's two-sum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float z = s - a;
+  e = (a - (s - z)) + (b - z);
+}
+
 struct BgemmParams {
   CUtensorMap ta[3];
   CUtensorMap tb[3];
   int M, N, K;
+  int tiles_n, ntiles, ksteps;
   int na, nb, npairs;
   int pair_a[6], pair_b[6];
   int a_mn;            // A MN-major
@@ -169,28 +182,40 @@ struct BgemmParams {
   unsigned* err;
 };
 
+// Persistent over output tiles (tile t -> rows (t / tiles_n) BM, columns
+// (t % tiles_n) BN).  The tensor-memory accumulator is drained every K step
+// of BK: the MMAs of one step start a fresh accumulator in one of two TMEM
+// buffers, and the epilogue warps add the step's result into a running sum
+// held in registers as an unevaluated FP32 pair (s, c) with a two-sum.  The
+// accumulation inside the tensor core adds each K = 16 product into FP32
+// with a bias, so its error grows like (K / 16) ulp; drained every 64 it
+// stays within a few ulp, and the running sum is exact to about FP32^2.
+// The MMA warp fills one buffer while the other is drained, and the
+// epilogue's output of one tile overlaps the main loop of the next.
 __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant__ BgemmParams p) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned tile area
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int per_stage = (p.na + p.nb) * TILE_BYTES;
+  const int per_stage = p.na * A_TILE + p.nb * B_TILE;
   uint64_t* full = (uint64_t*)(smem + (size_t)p.stages * per_stage);
   uint64_t* empty = full + p.stages;
-  uint64_t* acc_full = empty + p.stages;
-  uint64_t* mma_done = acc_full + 1;
+  uint64_t* acc_full = empty + p.stages;  // [2]
+  uint64_t* acc_empty = acc_full + 2;     // [2]
+  uint64_t* mma_done = acc_empty + 2;
   uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // N tiles vary fastest so the CTAs that share an A tile run together (L2 reuse)
-  const int n0 = blockIdx.x * BN, m0 = blockIdx.y * BM;
-  const int ksteps = (p.K + BK - 1) / BK;
+  const int ksteps = p.ksteps;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(acc_full, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+    }
     mbar_init(mma_done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -208,113 +233,159 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int issued = 0;
-      for (int ks = 0; ks < ksteps; ++ks) {
-        const int s = ks % p.stages;
-        const int round = ks / p.stages;
-        if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), p.err, 11)) break;
-        uint8_t* st = smem + (size_t)s * per_stage;
-        mbar_expect_tx(&full[s], (uint32_t)per_stage);
-        const int k0 = ks * BK;
-        for (int i = 0; i < p.na; ++i) {
-          uint8_t* dst = st + i * TILE_BYTES;
-          if (p.a_mn) {
-            tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + m0, p.a_y0 + k0);
-            tma_load_2d(dst + TILE_BYTES / 2, &p.ta[i], &full[s], p.a_x0 + m0 + 64, p.a_y0 + k0);
-          } else {
-            tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + k0, p.a_y0 + m0);
+      int g = 0;  // K steps issued over all tiles of this CTA
+      bool run = true;
+      for (int tile = blockIdx.x; run && tile < p.ntiles; tile += gridDim.x) {
+        const int m0 = (tile / p.tiles_n) * BM, n0 = (tile % p.tiles_n) * BN;
+        for (int ks = 0; ks < ksteps; ++ks, ++g) {
+          const int s = g % p.stages;
+          const int round = g / p.stages;
+          if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), p.err, 11)) {
+            run = false;
+            break;
+          }
+          uint8_t* st = smem + (size_t)s * per_stage;
+          mbar_expect_tx(&full[s], (uint32_t)per_stage);
+          const int k0 = ks * BK;
+          for (int i = 0; i < p.na; ++i) {
+            uint8_t* dst = st + i * A_TILE;
+            if (p.a_mn) {
+              tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + m0, p.a_y0 + k0);
+              tma_load_2d(dst + A_TILE / 2, &p.ta[i], &full[s], p.a_x0 + m0 + 64, p.a_y0 + k0);
+            } else {
+              tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + k0, p.a_y0 + m0);
+            }
+          }
+          for (int j = 0; j < p.nb; ++j) {
+            uint8_t* dst = st + p.na * A_TILE + j * B_TILE;
+            tma_load_2d(dst, &p.tb[j], &full[s], p.b_x0 + k0, p.b_y0 + n0);
           }
         }
-        for (int j = 0; j < p.nb; ++j) {
-          uint8_t* dst = st + (p.na + j) * TILE_BYTES;
-          tma_load_2d(dst, &p.tb[j], &full[s], p.b_x0 + k0, p.b_y0 + n0);
-        }
-        issued = ks + 1;
       }
       // let every copy issued land before the CTA can exit
-      for (int ks = (issued > p.stages ? issued - p.stages : 0); ks < issued; ++ks) {
-        mbar_wait(&full[ks % p.stages], (uint32_t)((ks / p.stages) & 1), p.err, 12);
+      for (int k = (g > p.stages ? g - p.stages : 0); k < g; ++k) {
+        mbar_wait(&full[k % p.stages], (uint32_t)((k / p.stages) & 1), p.err, 12);
       }
     }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
     if (lane == 0) {
       const uint32_t idesc = instr_desc(p.a_mn);
-      // Two accumulators: the leading product A_0 B_0 in columns [0, BN) and
-      // the small correction products (about 2^-8 of it) in [BN, 2 BN).
-      // Adding the corrections to a separate, small running sum keeps the
-      // rounding of the large sum to one addition per K term, as in an FP32
-      // GEMM, instead of six.
-      uint32_t accum[2] = {0u, 0u};
-      for (int ks = 0; ks < ksteps; ++ks) {
-        const int s = ks % p.stages;
-        if (!mbar_wait(&full[s], (uint32_t)((ks / p.stages) & 1), p.err, 13)) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t st = smem_u32(smem + (size_t)s * per_stage);
-        for (int q = 0; q < p.npairs; ++q) {
-          const uint32_t a_addr = st + p.pair_a[q] * TILE_BYTES;
-          const uint32_t b_addr = st + (p.na + p.pair_b[q]) * TILE_BYTES;
-#pragma unroll
-          for (int kk = 0; kk < BK / 16; ++kk) {
-            uint64_t ad, bd;
-            if (p.a_mn) ad = smem_desc(a_addr + kk * 2048, TILE_BYTES / 2, 1024);
-            else        ad = smem_desc(a_addr + kk * 32, 16, 1024);
-            bd = smem_desc(b_addr + kk * 32, 16, 1024);
-            const int slot = (q == 0) ? 0 : 1;
-            mma_bf16(tmem + (uint32_t)(slot * BN), ad, bd, idesc, accum[slot]);
-            accum[slot] = 1;
+      int g = 0;
+      bool run = true;
+      for (int tile = blockIdx.x; run && tile < p.ntiles; tile += gridDim.x) {
+        for (int ks = 0; ks < ksteps; ++ks, ++g) {
+          const int buf = g & 1, use = g >> 1;
+          if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), p.err, 16)) {
+            run = false;
+            break;
           }
+          const int s = g % p.stages;
+          if (!mbar_wait(&full[s], (uint32_t)((g / p.stages) & 1), p.err, 13)) {
+            run = false;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t st = smem_u32(smem + (size_t)s * per_stage);
+          // Two accumulators per buffer: the leading product A_0 B_0 and the
+          // correction products (about 2^-8 of it), so that the large sum is
+          // rounded once per K term, as in an FP32 GEMM, instead of six times.
+          uint32_t accum[2] = {0u, 0u};
+          for (int q = 0; q < p.npairs; ++q) {
+            const uint32_t a_addr = st + p.pair_a[q] * A_TILE;
+            const uint32_t b_addr = st + p.na * A_TILE + p.pair_b[q] * B_TILE;
+            const int slot = (q == 0) ? 0 : 1;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              uint64_t ad;
+              if (p.a_mn) ad = smem_desc(a_addr + kk * 2048, A_TILE / 2, 1024);
+              else        ad = smem_desc(a_addr + kk * 32, 16, 1024);
+              const uint64_t bd = smem_desc(b_addr + kk * 32, 16, 1024);
+              mma_bf16(tmem + (uint32_t)((buf * 2 + slot) * BN), ad, bd, idesc, accum[slot]);
+              accum[slot] = 1;
+            }
+          }
+          mma_commit(&empty[s]);         // stage s is free once these MMAs have read it
+          mma_commit(&acc_full[buf]);    // and the step's result is in buffer buf
         }
-        mma_commit(&empty[s]);  // stage s is free once these MMAs have read it
       }
-      mma_commit(acc_full);
       mma_commit(mma_done);
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int q = warp & 3;  // TMEM lane quadrant this warp may access
-    const bool ok = mbar_wait(acc_full, 0, p.err, 14);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    if (ok && *(volatile unsigned*)p.err == 0) {
-      const int row = m0 + q * 32 + lane;
-      for (int c = 0; c < BN; c += 32) {
-        float v[32];
-        tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-        if (p.npairs > 1) {
-          float lo[32];
-          tmem_ld32(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(BN + c), lo);
+    const int qd = warp & 3;  // TMEM lane quadrant this warp may access
+    const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
+    int g = 0;
+    bool ok = true;
+    for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
+      const int m0 = (tile / p.tiles_n) * BM, n0 = (tile % p.tiles_n) * BN;
+      float sum[BN], cmp[BN];
 #pragma unroll
-          for (int i = 0; i < 32; ++i) v[i] += lo[i];
+      for (int i = 0; i < BN; ++i) { sum[i] = 0.f; cmp[i] = 0.f; }
+      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+        const int buf = g & 1, use = g >> 1;
+        bool w = mbar_wait(&acc_full[buf], (uint32_t)(use & 1), p.err, 14);
+        ok = __all_sync(0xffffffffu, w) && ok;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int cc = 0; cc < BN; cc += 32) {
+          float v[32];
+          tmem_ld32(tmem + lane_base + (uint32_t)(buf * 2 * BN + cc), v);
+          if (p.npairs > 1) {
+            float lo[32];
+            tmem_ld32(tmem + lane_base + (uint32_t)((buf * 2 + 1) * BN + cc), lo);
+#pragma unroll
+            for (int i = 0; i < 32; ++i) v[i] += lo[i];
+          }
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            float t, e;
+            two_sum(sum[cc + i], v[i], t, e);
+            sum[cc + i] = t;
+            cmp[cc + i] += e;
+          }
         }
-        if (row < p.M) {
-          if (p.mode == 0) {
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      }
+      // warp-uniform: the lanes must not split before the next tcgen05.ld
+      if (__any_sync(0xffffffffu, !ok || *(volatile unsigned*)p.err != 0)) break;
+      const int row = m0 + qd * 32 + lane;
+      if (row < p.M) {
+        if (p.mode == 0) {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int col = n0 + c + i;
-              if (col < p.N) {
-                float* dst = p.C + (int64_t)row + (int64_t)col * p.ldc;
-                float r = p.alpha * v[i];
-                if (p.beta != 0.f) r = fmaf(p.beta, *dst, r);
-                *dst = r;
-              }
+          for (int i = 0; i < BN; ++i) {
+            const int col = n0 + i;
+            if (col < p.N) {
+              float* dst = p.C + (int64_t)row + (int64_t)col * p.ldc;
+              float r = p.alpha * (sum[i] + cmp[i]);
+              if (p.beta != 0.f) r = fmaf(p.beta, *dst, r);
+              *dst = r;
             }
-          } else {
+          }
+        } else {
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-              const int col = n0 + c + i;
-              if (col < p.N) {
-                const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
-                const float x = __bfloat162float(p.P0[o]) + __bfloat162float(p.P1[o]) +
-                                __bfloat162float(p.P2[o]);
-                const float y = fmaf(p.alpha, v[i], x);
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(y);
-                const float r1 = y - __bfloat162float(h0);
-                const __nv_bfloat16 h1 = __float2bfloat16_rn(r1);
-                const __nv_bfloat16 h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
-                p.P0[o] = h0;
-                p.P1[o] = h1;
-                p.P2[o] = h2;
-              }
+          for (int i = 0; i < BN; ++i) {
+            const int col = n0 + i;
+            if (col < p.N) {
+              const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
+              // X + alpha acc carried as hi + lo, then split into three planes
+              const float x0 = __bfloat162float(p.P0[o]);
+              const float xr = __bfloat162float(p.P1[o]) + __bfloat162float(p.P2[o]);
+              float hi, lo;
+              two_sum(x0, p.alpha * sum[i], hi, lo);
+              lo += xr + p.alpha * cmp[i];
+              float y, ey;
+              two_sum(hi, lo, y, ey);
+              const __nv_bfloat16 h0 = __float2bfloat16_rn(y);
+              const float r = (y - __bfloat162float(h0)) + ey;
+              const __nv_bfloat16 h1 = __float2bfloat16_rn(r);
+              const __nv_bfloat16 h2 = __float2bfloat16_rn(r - __bfloat162float(h1));
+              p.P0[o] = h0;
+              p.P1[o] = h1;
+              p.P2[o] = h2;
             }
           }
         }
@@ -372,6 +443,7 @@ int make_tmap_bf16(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, in
 int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int K, int pairs_mode,
                  const BgemmOut& out, unsigned* err, cudaStream_t st) {
   if (M <= 0 || N <= 0) return 0;
+  if (K <= 0) return RANDUTV_EUNSUPPORTED;  // no product to accumulate
   BgemmParams p;
   memset(&p, 0, sizeof p);
   p.na = A.nplanes;
@@ -382,7 +454,7 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
     RUTV_TRY(make_tmap_bf16(&p.ta[i], A.planes[i], A.rows, A.cols, A.ld, A.mn_major ? 64 : 128));
   }
   for (int j = 0; j < p.nb; ++j) {
-    RUTV_TRY(make_tmap_bf16(&p.tb[j], B.planes[j], B.rows, B.cols, B.ld, 128));
+    RUTV_TRY(make_tmap_bf16(&p.tb[j], B.planes[j], B.rows, B.cols, B.ld, BN));
   }
   p.M = M;
   p.N = N;
@@ -402,9 +474,9 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.a_y0 = (int)A.y0;
   p.b_x0 = (int)B.x0;
   p.b_y0 = (int)B.y0;
-  const int per_stage = (p.na + p.nb) * TILE_BYTES;
-  int stages = (200 * 1024) / per_stage;
-  if (stages > 6) stages = 6;
+  const int per_stage = p.na * A_TILE + p.nb * B_TILE;
+  int stages = (216 * 1024) / per_stage;
+  if (stages > 8) stages = 8;
   if (stages < 1) stages = 1;
   p.stages = stages;
   p.mode = out.mode;
@@ -417,14 +489,19 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.P2 = out.planes[2];
   p.ldp = out.ldp;
   p.err = err;
-  const size_t smem = 1024 + (size_t)stages * per_stage + (2 * stages + 2) * 8 + 16;
+  const int tiles_m = (M + BM - 1) / BM;
+  p.tiles_n = (N + BN - 1) / BN;
+  p.ntiles = tiles_m * p.tiles_n;
+  p.ksteps = (K + BK - 1) / BK;
+  const size_t smem = 1024 + (size_t)stages * per_stage + (2 * stages + 5) * 8 + 16;
   static size_t configured = 0;
   if (smem > configured) {
     RUTV_CK(cudaFuncSetAttribute(bgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)smem));
     configured = smem;
   }
-  dim3 grid((unsigned)((N + BN - 1) / BN), (unsigned)((M + BM - 1) / BM));
+  // persistent: at most one CTA per SM (the shared memory allows no more)
+  const int grid = p.ntiles < dev_info().sms ? p.ntiles : dev_info().sms;
   ProfScope prof(K_BGEMM, 2.0 * M * (double)N * K * p.npairs,
                  2.0 * ((double)M * K * p.na + (double)K * N * p.nb) +
                      (out.mode == 0 ? 4.0 : 12.0) * M * (double)N,

@@ -1,50 +1,78 @@
 // SVD of the b x b diagonal block (Fig. 2: [A11, U_SVD, V_SVD] := SVD(A11);
-// §3.1 step 3), one-sided Jacobi in FP64 (Hestenes 1958; Demmel & Veselic
-// 1992 for the rotation and the stopping rule).
+// §3.1 step 3) by one-sided Jacobi (Hestenes 1958; Demmel & Veselic 1992 for
+// the rotation and the stopping rule), in two phases:
 //
-// Layout: one thread-block cluster of C CTAs (16 where the device can place
-// that non-portable size, else 8).  CTA k holds rows [k R, (k+1) R) of both
-// the working matrix B (which converges to U diag(D)) and the accumulated
-// rotation V, R = ceil(b/C), in shared memory.  A sweep is b-1 rounds of the
-// round-robin (circle) ordering, each round rotating b/2 disjoint column
-// pairs.  Per round every CTA writes the partial inner products
-// (|a_p|^2, |a_q|^2, a_p.a_q) of its rows, a cluster barrier follows, and
-// every CTA combines the C partials of each pair in a fixed order through
-// distributed shared memory.  The rotation parameters are therefore bitwise
-// identical in all CTAs, which apply them to their own rows, and all CTAs
-// take the same convergence decision.  FP64 throughput per SM is low on this
-// part (two DFMA per clock), which is why the rows are spread over C SMs.
+//   1. FP32 sweeps on B (scaled by a power of two into the FP32 range) until
+//      its columns are orthogonal to FP32 accuracy, the rotations accumulated
+//      in V32.  FP32 runs at 64 times the FP64 rate of this part, and the
+//      sweeps that take a dense block to near-orthogonal columns are most of
+//      the work.
+//   2. V32 is made orthogonal to FP64 accuracy by two Newton-Schulz steps
+//      V <- V (3I - V^T V) / 2 (FP64 products), C = B V in FP64, and FP64
+//      sweeps on C that start from V finish the job.  The columns of C are
+//      already orthogonal to about 1e-6, so Jacobi's quadratic convergence
+//      reaches FP64 accuracy within two or three sweeps.  Stopping rule and
+//      outputs are those of a plain FP64 one-sided Jacobi, so the result does
+//      not depend on phase 1 beyond rounding.
+// Blocks of at most 32 columns skip phase 1.
 //
-// After convergence: D_j = |b_j|, columns sorted by descending D (lowest
-// index first on ties), U_j = b_j / D_j, and each column of V signed so that
-// its entry of largest magnitude (lowest row on ties) is positive, U_j with
-// it.  Exactly-zero singular values get their U columns from a separate
+// Both phases run one kernel, templated on the arithmetic type, on one
+// thread-block cluster of C CTAs.  CTA k holds rows [k R, (k+1) R) of the
+// working matrix and of V in shared memory.  A sweep is b-1 rounds of the
+// round-robin (circle) ordering, each rotating b/2 disjoint column pairs:
+//   * every CTA writes the partial inner products (|a_p|^2, |a_q|^2, a_p.a_q)
+//     of its rows for all pairs; cluster barrier;
+//   * CTA k owns pairs [k ceil(npairs/C), (k+1) ceil(npairs/C)): it sums their
+//     C partials in a fixed order through distributed shared memory, computes
+//     the rotations and stores them into every CTA; cluster barrier;
+//   * every CTA applies all the rotations to its own rows.
+// Each rotation is computed once, so it is bitwise identical in every CTA, and
+// each CTA moves O(npairs) words through the cluster per round (pulling every
+// pair's partials into every CTA would move O(npairs C)).
+//
+// After phase 2: D_j = |c_j|, columns sorted by descending D (lowest index
+// first on ties), U_j = c_j / D_j, and each column of V signed so that its
+// entry of largest magnitude (lowest row on ties) is positive, U_j with it.
+// Exactly-zero singular values get their U columns from a separate
 // completion kernel (Gram-Schmidt of unit vectors).
 #include <cooperative_groups.h>
 
 #include "common.cuh"
+#include "kernels.h"
 
 namespace cg = cooperative_groups;
 
 namespace rutv {
 
 namespace {
-constexpr int SVD_CL = 8;
 constexpr int SVD_THREADS = 256;
 constexpr int SVD_MAX_B = 256;
+constexpr int SVD_DIRECT_B = 32;  // blocks up to this size skip the FP32 phase
 
-struct SvdSmem {
-  int b, P, npairs, R, LDR;
-  size_t bytes() const {
-    size_t d = 2 * (size_t)P * LDR          // Bl, Vl
-               + 2 * (size_t)npairs * 3     // partials, double buffered
-               + (size_t)P                  // column norms (partial)
-               + (size_t)P                  // max |V| per column, signed (partial)
-               + (size_t)P                  // max |V| per column, signed (cluster)
-               + (size_t)P;                 // D (full)
-    return d * sizeof(double) + (size_t)P * sizeof(int) * 2 + 64;
-  }
+struct JacArgs {
+  int b;
+  const double* B;   // input block (FP64), column-major
+  int64_t ldb;
+  const double* Vin; // initial V (b x b, ld b), or null for the identity
+  float* V32;        // phase 1 output: V (b x b, ld b)
+  double* D;         // phase 2 outputs
+  double* Us;
+  double* Vs;
+  int max_sweeps;
+  double tol;        // rotate while |a_p.a_q| > tol |a_p| |a_q|
+  unsigned* info;    // phase 2: sweeps taken
 };
+
+template <typename Real>
+size_t jac_smem_bytes(int b, int ncl) {
+  const int P = (b + 1) & ~1, npairs = P / 2, R = (b + ncl - 1) / ncl, LDR = R + 1;
+  return 4 * (size_t)P * sizeof(double)                                  // norms, vmax, vbest, D
+         + (2 * (size_t)P * LDR + 5 * (size_t)npairs) * sizeof(Real)     // B, V, partials, rotations
+         + 2 * (size_t)P * sizeof(int) + 64;                             // vrow, rankof
+}
+
+__device__ __forceinline__ float fmar(float x, float y, float z) { return fmaf(x, y, z); }
+__device__ __forceinline__ double fmar(double x, double y, double z) { return fma(x, y, z); }
 
 __device__ __forceinline__ void rr_pair(int round, int t, int P, int* p, int* q) {
   int a, c;
@@ -59,74 +87,96 @@ __device__ __forceinline__ void rr_pair(int round, int t, int P, int* p, int* q)
   *q = a < c ? c : a;
 }
 
-__global__ void __launch_bounds__(SVD_THREADS)
-jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __restrict__ D,
-                  double* __restrict__ Us, double* __restrict__ Vs, int max_sweeps,
-                  unsigned* __restrict__ info) {
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double m = 0.0;
+  for (int w = 0; w < SVD_THREADS / 32; ++w) m = fmax(m, red[w]);
+  __syncthreads();
+  return m;
+}
+
+template <typename Real, bool kFinal>
+__global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
-  SvdSmem L;
-  L.b = b;
-  L.P = (b + 1) & ~1;
-  L.npairs = L.P / 2;
-  const int ncl = (int)cl.num_blocks();  // 16 where the device allows it, else 8
-  L.R = (b + ncl - 1) / ncl;
-  L.LDR = L.R + 1;
-  const int P = L.P, npairs = L.npairs, R = L.R, LDR = L.LDR;
+  const int ncl = (int)cl.num_blocks();
+  const int b = a.b, P = (b + 1) & ~1, npairs = P / 2;
+  const int R = (b + ncl - 1) / ncl, LDR = R + 1;
   const int r0 = rank * R;
   const int nr = max(0, min(b, r0 + R) - r0);
+  const int tid = threadIdx.x;
 
   extern __shared__ double smem[];
-  double* Bl = smem;                       // column j, local row i at Bl[j*LDR + i]
-  double* Vl = Bl + (size_t)P * LDR;
-  double* part = Vl + (size_t)P * LDR;     // [2][npairs][3]
-  double* npart = part + 2 * npairs * 3;   // [P]
-  double* vmax = npart + P;                // [P]
-  double* vbest = vmax + P;                // [P]
-  double* Dfull = vbest + P;               // [P]
-  int* vrow = (int*)(Dfull + P);           // [P]
-  int* rankof = vrow + P;                  // [P]
+  double* npart = smem;               // [P] column norms^2 of own rows
+  double* vmax = npart + P;           // [P] signed entry of largest |V| in own rows
+  double* vbest = vmax + P;           // [P] same, over the cluster
+  double* Dfull = vbest + P;          // [P]
+  Real* Bl = reinterpret_cast<Real*>(Dfull + P);  // column j, local row i at Bl[j*LDR + i]
+  Real* Vl = Bl + (size_t)P * LDR;
+  Real* part = Vl + (size_t)P * LDR;  // [npairs][3]
+  Real* rot = part + (size_t)npairs * 3;  // [npairs][2]: (c, s)
+  int* vrow = reinterpret_cast<int*>(rot + (size_t)npairs * 2);
+  int* rankof = vrow + P;
   __shared__ int s_rotated;
+  __shared__ double s_red[SVD_THREADS / 32];
 
-  // load own rows of B, V = I (padding column b, if any, is zero)
-  for (int e = threadIdx.x; e < P * LDR; e += SVD_THREADS) {
+  // Phase 1 works on B 2^-e, e the exponent of max |B| (exact, and inside
+  // the FP32 range whatever the scale of the block).
+  double scale = 1.0;
+  if (!kFinal) {
+    double mx = 0.0;
+    for (int e = tid; e < b * b; e += SVD_THREADS)
+      mx = fmax(mx, fabs(a.B[(e % b) + (int64_t)(e / b) * a.ldb]));
+    mx = block_max(mx, s_red);
+    if (mx > 0.0) {
+      int ex = 0;
+      frexp(mx, &ex);
+      scale = ldexp(1.0, -ex);
+    }
+  }
+  for (int e = tid; e < P * LDR; e += SVD_THREADS) {
     const int j = e / LDR, i = e % LDR;
     const int gi = r0 + i;
     double bv = 0.0, vv = 0.0;
     if (i < nr && j < b) {
-      bv = Bg[gi + (int64_t)j * ldb];
-      vv = (gi == j) ? 1.0 : 0.0;
+      bv = a.B[gi + (int64_t)j * a.ldb] * scale;
+      vv = a.Vin ? a.Vin[gi + (int64_t)j * b] : ((gi == j) ? 1.0 : 0.0);
     }
-    Bl[e] = bv;
-    Vl[e] = vv;
+    Bl[e] = (Real)bv;
+    Vl[e] = (Real)vv;
   }
-  if (threadIdx.x == 0) s_rotated = 0;
-  __syncthreads();
+  if (tid == 0) s_rotated = 0;
+  cl.sync();
 
   int tpp = 1;
   while (tpp < 32 && tpp * 2 * npairs <= SVD_THREADS) tpp *= 2;
-  const int g = threadIdx.x / tpp, sub = threadIdx.x % tpp;
+  const int g = tid / tpp, sub = tid % tpp;
   const bool active = g < npairs;
-  const double tol = (double)(b > 1 ? b : 1) * 0x1.0p-53;
+  int NS = 1;
+  while (NS < ncl) NS <<= 1;
+  const int ppc = (npairs + ncl - 1) / ncl;  // pairs owned per CTA; ppc * NS <= 2 npairs <= 256
+  const int own_pl = tid / NS, own_src = tid % NS;
+  const int own_pair = rank * ppc + own_pl;
+  const bool own_lane = tid < ppc * NS && own_pair < npairs;
+  const double tol = a.tol;
 
   int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
+  for (; sweep < a.max_sweeps; ++sweep) {
     for (int round = 0; round < P - 1; ++round) {
-      // Parity of the running round count (a sweep has an odd number of
-      // rounds, so the round index alone would reuse a buffer back to back).
-      const int buf = (int)(((unsigned)sweep * (unsigned)(P - 1) + (unsigned)round) & 1u);
       int p = 0, q = 0;
       if (active) rr_pair(round, g, P, &p, &q);
       // partial inner products over own rows
-      double sa = 0.0, sb = 0.0, sc = 0.0;
+      Real sa = 0, sb = 0, sc = 0;
       if (active) {
-        const double* bp = Bl + (size_t)p * LDR;
-        const double* bq = Bl + (size_t)q * LDR;
+        const Real* bp = Bl + (size_t)p * LDR;
+        const Real* bq = Bl + (size_t)q * LDR;
         for (int i = sub; i < nr; i += tpp) {
-          const double x = bp[i], y = bq[i];
-          sa = fma(x, x, sa);
-          sb = fma(y, y, sb);
-          sc = fma(x, y, sc);
+          const Real x = bp[i], y = bq[i];
+          sa = fmar(x, x, sa);
+          sb = fmar(y, y, sb);
+          sc = fmar(x, y, sc);
         }
       }
       for (int o = tpp >> 1; o > 0; o >>= 1) {
@@ -135,93 +185,111 @@ jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __r
         sc += __shfl_xor_sync(0xffffffffu, sc, o);
       }
       if (active && sub == 0) {
-        double* pp = part + ((size_t)buf * npairs + g) * 3;
-        pp[0] = sa; pp[1] = sb; pp[2] = sc;
+        part[(size_t)g * 3] = sa;
+        part[(size_t)g * 3 + 1] = sb;
+        part[(size_t)g * 3 + 2] = sc;
       }
       cl.sync();
-      // cluster sums in CTA order, rotation parameters
-      // The threads of the group load the 8 CTAs' partials in parallel and
-      // combine them with a fixed shuffle tree: every thread (of every CTA)
-      // ends with the same sums and takes the same rotation.
-      double c = 1.0, s = 0.0;
-      int rot = 0;
+      // owned pairs: sum the partials of all CTAs (fixed shuffle tree, so every
+      // lane of the group ends with the same sums) and broadcast the rotation
       {
         double al = 0.0, be = 0.0, ga = 0.0;
-        if (active) {
-          for (int k = sub; k < ncl; k += tpp) {
-            const double* rp = cl.map_shared_rank(part, k) + ((size_t)buf * npairs + g) * 3;
-            al += rp[0];
-            be += rp[1];
-            ga += rp[2];
-          }
+        if (own_lane && own_src < ncl) {
+          const Real* rp = cl.map_shared_rank(part, own_src) + (size_t)own_pair * 3;
+          al = (double)rp[0];
+          be = (double)rp[1];
+          ga = (double)rp[2];
         }
-        for (int o = tpp >> 1; o > 0; o >>= 1) {
+        for (int o = NS >> 1; o > 0; o >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, o);
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        if (active && q < b && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-          const double zeta = (be - al) / (2.0 * ga);
-          const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-          c = 1.0 / sqrt(fma(t, t, 1.0));
-          s = c * t;
-          rot = 1;
+        double c = 1.0, s = 0.0;
+        if (own_lane) {
+          int pp, qq;
+          rr_pair(round, own_pair, P, &pp, &qq);
+          if (qq < b && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
+            const double zeta = (be - al) / (2.0 * ga);
+            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+            c = 1.0 / sqrt(fma(t, t, 1.0));
+            s = c * t;
+          }
+        }
+        if (own_lane && own_src < ncl) {
+          Real* rr = cl.map_shared_rank(rot, own_src) + (size_t)own_pair * 2;
+          rr[0] = (Real)c;
+          rr[1] = (Real)s;
+          if (own_src == 0 && s != 0.0) s_rotated = 1;
         }
       }
-      if (active && rot) {
-        if (sub == 0) s_rotated = 1;
-        double* bp = Bl + (size_t)p * LDR;
-        double* bq = Bl + (size_t)q * LDR;
-        for (int i = sub; i < nr; i += tpp) {
-          const double x = bp[i], y = bq[i];
-          bp[i] = fma(c, x, -s * y);
-          bq[i] = fma(s, x, c * y);
-        }
-        double* vp = Vl + (size_t)p * LDR;
-        double* vq = Vl + (size_t)q * LDR;
-        for (int i = sub; i < nr; i += tpp) {
-          const double x = vp[i], y = vq[i];
-          vp[i] = fma(c, x, -s * y);
-          vq[i] = fma(s, x, c * y);
+      cl.sync();
+      if (active) {
+        const Real c = rot[(size_t)g * 2], s = rot[(size_t)g * 2 + 1];
+        if (s != (Real)0) {
+          Real* bp = Bl + (size_t)p * LDR;
+          Real* bq = Bl + (size_t)q * LDR;
+          for (int i = sub; i < nr; i += tpp) {
+            const Real x = bp[i], y = bq[i];
+            bp[i] = fmar(c, x, -s * y);
+            bq[i] = fmar(s, x, c * y);
+          }
+          Real* vp = Vl + (size_t)p * LDR;
+          Real* vq = Vl + (size_t)q * LDR;
+          for (int i = sub; i < nr; i += tpp) {
+            const Real x = vp[i], y = vq[i];
+            vp[i] = fmar(c, x, -s * y);
+            vq[i] = fmar(s, x, c * y);
+          }
         }
       }
       __syncthreads();
     }
-    const int any = s_rotated;
-    __syncthreads();
-    if (threadIdx.x == 0) s_rotated = 0;
-    __syncthreads();
+    // every CTA reads every owner's flag: the same decision everywhere
+    int any = 0;
+    for (int k = 0; k < ncl; ++k) any |= *cl.map_shared_rank(&s_rotated, k);
+    cl.sync();  // all flags read before any is reset
+    if (tid == 0) s_rotated = 0;
     if (!any) break;
   }
 
+  if (!kFinal) {
+    if (rank == 0 && tid == 0 && a.info) a.info[0] = (unsigned)sweep;
+    for (int e = tid; e < b * nr; e += SVD_THREADS) {
+      const int j = e / nr, i = e % nr;
+      a.V32[(r0 + i) + (int64_t)j * b] = (float)Vl[(size_t)j * LDR + i];
+    }
+    return;  // no CTA reads another's shared memory after the last cluster barrier
+  }
+
   // column norms and the signed entry of largest |V| per column (own rows)
-  for (int j = threadIdx.x; j < P; j += SVD_THREADS) {
+  for (int j = tid; j < P; j += SVD_THREADS) {
     double s2 = 0.0, bestabs = -1.0;
     int bi = 0;
     for (int i = 0; i < nr; ++i) {
-      const double x = Bl[(size_t)j * LDR + i];
+      const double x = (double)Bl[(size_t)j * LDR + i];
       s2 = fma(x, x, s2);
-      const double a = fabs(Vl[(size_t)j * LDR + i]);
-      if (a > bestabs) {  // strict: lowest row wins ties
-        bestabs = a;
+      const double av = fabs((double)Vl[(size_t)j * LDR + i]);
+      if (av > bestabs) {  // strict: lowest row wins ties
+        bestabs = av;
         bi = i;
       }
     }
     npart[j] = s2;
-    vmax[j] = (nr > 0) ? Vl[(size_t)j * LDR + bi] : 0.0;
+    vmax[j] = (nr > 0) ? (double)Vl[(size_t)j * LDR + bi] : 0.0;
     vrow[j] = r0 + bi;
   }
   cl.sync();
-  for (int j = threadIdx.x; j < P; j += SVD_THREADS) {
+  for (int j = tid; j < P; j += SVD_THREADS) {
     // The running maximum keeps its magnitude and its owner explicitly; the
     // signed value is fetched from the owning CTA once the winner is known.
     double s2 = 0.0, bestabs = -1.0;
     int bestk = 0;
     for (int k = 0; k < ncl; ++k) {
       s2 += cl.map_shared_rank(npart, k)[j];
-      const double a = fabs(cl.map_shared_rank(vmax, k)[j]);
-      if (a > bestabs) {  // strict: lower rows (CTAs) win ties
-        bestabs = a;
+      const double av = fabs(cl.map_shared_rank(vmax, k)[j]);
+      if (av > bestabs) {  // strict: lower rows (CTAs) win ties
+        bestabs = av;
         bestk = k;
       }
     }
@@ -229,7 +297,7 @@ jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __r
     vbest[j] = cl.map_shared_rank(vmax, bestk)[j];
   }
   cl.sync();  // every CTA has finished reading the others' vmax/npart
-  for (int j = threadIdx.x; j < b; j += SVD_THREADS) {
+  for (int j = tid; j < b; j += SVD_THREADS) {
     const double dj = Dfull[j];
     int rk = 0;
     for (int l = 0; l < b; ++l) {
@@ -240,20 +308,19 @@ jacobi_svd_kernel(int b, const double* __restrict__ Bg, int64_t ldb, double* __r
   }
   __syncthreads();
   // write outputs: column j goes to position rankof[j]
-  for (int e = threadIdx.x; e < b * nr; e += SVD_THREADS) {
+  for (int e = tid; e < b * nr; e += SVD_THREADS) {
     const int j = e / nr, i = e % nr;
     const int pos = rankof[j];
     const double sg = (vbest[j] < 0.0) ? -1.0 : 1.0;
     const double dj = Dfull[j];
     const int64_t gi = r0 + i;
-    Vs[gi + (int64_t)pos * b] = sg * Vl[(size_t)j * LDR + i];
-    Us[gi + (int64_t)pos * b] = (dj > 0.0) ? sg * (Bl[(size_t)j * LDR + i] / dj) : 0.0;
+    a.Vs[gi + (int64_t)pos * b] = sg * (double)Vl[(size_t)j * LDR + i];
+    a.Us[gi + (int64_t)pos * b] = (dj > 0.0) ? sg * ((double)Bl[(size_t)j * LDR + i] / dj) : 0.0;
   }
   if (rank == 0) {
-    for (int j = threadIdx.x; j < b; j += SVD_THREADS) D[rankof[j]] = Dfull[j];
-    if (threadIdx.x == 0 && info) info[0] = (unsigned)sweep;
+    for (int j = tid; j < b; j += SVD_THREADS) a.D[rankof[j]] = Dfull[j];
+    if (tid == 0 && a.info) a.info[0] = (unsigned)sweep;
   }
-  cl.sync();  // keep shared memory alive until no CTA reads it remotely
 }
 
 // Completes the columns of Us whose singular value is exactly zero: modified
@@ -291,54 +358,44 @@ __global__ void complete_basis_kernel(int b, const double* __restrict__ D, doubl
     }
   }
 }
-}  // namespace
 
-int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us, double* Vs,
-                     unsigned* info, cudaStream_t st) {
-  if (b < 1 || b > SVD_MAX_B) return RANDUTV_EUNSUPPORTED;
-  SvdSmem L;
-  L.b = b;
-  L.P = (b + 1) & ~1;
-  L.npairs = L.P / 2;
-  // A cluster of 16 CTAs (a non-portable size) halves each CTA's FP64 work
-  // per round; fall back to the portable 8 where the device cannot place 16.
-  static int ncl = 0;
-  static size_t configured = 0;
-  if (ncl == 0) {
-    RUTV_CK(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeNonPortableClusterSizeAllowed,
-                                 1));
-    RUTV_CK(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 160 * 1024));
-    configured = 160 * 1024;
-    cudaLaunchConfig_t cfg = {};
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = 16;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(16);
-    cfg.blockDim = dim3(SVD_THREADS);
-    cfg.dynamicSmemBytes = 100 * 1024;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int nclusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)jacobi_svd_kernel, &cfg) == cudaSuccess &&
-        nclusters > 0)
-      ncl = 16;
-    else
-      ncl = SVD_CL;
-    cudaGetLastError();
+// V <- (double) V32 and H <- I (both b x b, ld b)
+__global__ void svd_prep_kernel(int b, const float* __restrict__ V32, double* __restrict__ V,
+                                double* __restrict__ H) {
+  const int64_t total = (int64_t)b * b;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    if (V32) V[e] = (double)V32[e];
+    H[e] = (e % b == e / b) ? 1.0 : 0.0;
   }
-  L.R = (b + ncl - 1) / ncl;
-  L.LDR = L.R + 1;
-  const size_t smem = L.bytes();
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <typename Real, bool kFinal>
+int configure(int b, int ncl, size_t* smem_out) {
+  static size_t configured = 0;
+  static bool nonportable = false;
+  if (!nonportable) {
+    RUTV_CK(cudaFuncSetAttribute(jacobi_kernel<Real, kFinal>,
+                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    nonportable = true;
+  }
+  const size_t smem = jac_smem_bytes<Real>(b, ncl);
   if (smem > configured) {
-    RUTV_CK(cudaFuncSetAttribute(jacobi_svd_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
+    RUTV_CK(cudaFuncSetAttribute(jacobi_kernel<Real, kFinal>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     configured = smem;
   }
-  ProfScope prof(K_SVD, 0.0, 32.0 * (double)b * b, st);
-  const int max_sweeps = 40;
+  *smem_out = smem;
+  return 0;
+}
+
+template <typename Real, bool kFinal>
+int launch_jacobi(const JacArgs& a, int ncl, cudaStream_t st) {
+  size_t smem = 0;
+  RUTV_TRY((configure<Real, kFinal>(a.b, ncl, &smem)));
+  ProfScope prof(kFinal ? K_SVD : K_SVD32, 0.0, 2.0 * sizeof(Real) * (double)a.b * a.b, st);
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -351,9 +408,110 @@ int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us,
   cfg.stream = st;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  RUTV_CK(cudaLaunchKernelEx(&cfg, jacobi_svd_kernel, b, B, ldb, D, Us, Vs, max_sweeps, info));
+  RUTV_CK(cudaLaunchKernelEx(&cfg, jacobi_kernel<Real, kFinal>, a));
   note_launch();
   RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
+// Cluster size of the FP64 phase: 16 CTAs (a non-portable size) where the
+// device can place them, else the portable 8.
+int fp64_cluster() {
+  static int ncl = 0;
+  if (ncl) return ncl;
+  size_t smem = 0;
+  if (configure<double, true>(SVD_MAX_B, 16, &smem) != 0) return 8;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = 16;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(16);
+  cfg.blockDim = dim3(SVD_THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  int nclusters = 0;
+  if (cudaOccupancyMaxActiveClusters(&nclusters, (void*)jacobi_kernel<double, true>, &cfg) ==
+          cudaSuccess &&
+      nclusters > 0)
+    ncl = 16;
+  else
+    ncl = 8;
+  cudaGetLastError();
+  return ncl;
+}
+
+// Smallest cluster whose FP32 share of B and V fits in shared memory.
+int fp32_cluster(int b) {
+  for (int c = 1; c < 16; c *= 2)
+    if (jac_smem_bytes<float>(b, c) <= 200 * 1024) return c;
+  return 16;
+}
+}  // namespace
+
+size_t small_svd_scratch_bytes(int b) {
+  return align256((size_t)b * b * sizeof(float)) + 2 * align256((size_t)b * b * sizeof(double));
+}
+
+int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us, double* Vs,
+                     unsigned* info, void* scratch, double* gemm_scratch, size_t gemm_bytes,
+                     cudaStream_t st) {
+  if (b < 1 || b > SVD_MAX_B) return RANDUTV_EUNSUPPORTED;
+  JacArgs a = {};
+  a.b = b;
+  a.D = D;
+  a.Us = Us;
+  a.Vs = Vs;
+  a.info = info;
+  a.max_sweeps = 40;
+  a.tol = (double)b * 0x1.0p-53;
+  if (b <= SVD_DIRECT_B) {
+    a.B = B;
+    a.ldb = ldb;
+    a.Vin = nullptr;
+    RUTV_TRY((launch_jacobi<double, true>(a, fp64_cluster(), st)));
+  } else {
+    char* s = (char*)scratch;
+    float* V32 = (float*)s;
+    double* H = (double*)(s + align256((size_t)b * b * sizeof(float)));
+    double* Vb = (double*)((char*)H + align256((size_t)b * b * sizeof(double)));
+    // phase 1: FP32 sweeps down to the FP32 noise level
+    JacArgs a1 = {};
+    a1.b = b;
+    a1.B = B;
+    a1.ldb = ldb;
+    a1.V32 = V32;
+    a1.max_sweeps = 20;
+    a1.tol = 2.0 * (double)b * 0x1.0p-24;
+    a1.info = info ? info + 1 : nullptr;
+    RUTV_TRY((launch_jacobi<float, false>(a1, fp32_cluster(b), st)));
+    // two Newton-Schulz steps: V <- V H, H = 1.5 I - 0.5 V^T V (FP64)
+    const int grid = (b * b + 255) / 256;
+    svd_prep_kernel<<<grid, 256, 0, st>>>(b, V32, Vs, H);
+    note_launch();
+    RUTV_CK(cudaGetLastError());
+    RUTV_TRY(launch_dgemm(true, false, b, b, b, -0.5, Vs, b, Vs, b, 1.5, H, b, gemm_scratch,
+                          gemm_bytes, st));
+    RUTV_TRY(launch_dgemm(false, false, b, b, b, 1.0, Vs, b, H, b, 0.0, Vb, b, gemm_scratch,
+                          gemm_bytes, st));
+    svd_prep_kernel<<<grid, 256, 0, st>>>(b, nullptr, nullptr, H);
+    note_launch();
+    RUTV_CK(cudaGetLastError());
+    RUTV_TRY(launch_dgemm(true, false, b, b, b, -0.5, Vb, b, Vb, b, 1.5, H, b, gemm_scratch,
+                          gemm_bytes, st));
+    RUTV_TRY(launch_dgemm(false, false, b, b, b, 1.0, Vb, b, H, b, 0.0, Vs, b, gemm_scratch,
+                          gemm_bytes, st));
+    // C = B V into Us; phase 2 reads C and V from Us and Vs and writes its
+    // outputs over them (every CTA reads and writes only its own rows)
+    RUTV_TRY(launch_dgemm(false, false, b, b, b, 1.0, B, ldb, Vs, b, 0.0, Us, b, gemm_scratch,
+                          gemm_bytes, st));
+    a.B = Us;
+    a.ldb = b;
+    a.Vin = Vs;
+    RUTV_TRY((launch_jacobi<double, true>(a, fp64_cluster(), st)));
+  }
   complete_basis_kernel<<<1, SVD_THREADS, 0, st>>>(b, D, Us);
   note_launch();
   RUTV_CK(cudaGetLastError());

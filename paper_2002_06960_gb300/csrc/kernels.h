@@ -21,7 +21,10 @@ int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* 
                           char* scratch, unsigned* bar, unsigned* err, cudaStream_t st);
 int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st);
 
+// Scratch of launch_small_svd (beside the dgemm scratch it also takes).
+size_t small_svd_scratch_bytes(int b);
 int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us, double* Vs,
-                     unsigned* info, cudaStream_t st);
+                     unsigned* info, void* scratch, double* gemm_scratch, size_t gemm_bytes,
+                     cudaStream_t st);
 
 }  // namespace rutv

@@ -107,6 +107,7 @@ struct MixedWork {
   float *Y, *Z, *X, *tmp, *scal;
   double *Y64, *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64, *WS64;
   char* qr;
+  char* svd;
   double* dgemm;
   size_t dgemm_bytes;
 };
@@ -146,6 +147,7 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add((size_t)b * 8 * 2);         // tau, D
   for (int i = 0; i < 5; ++i) add((size_t)b * b * 8);    // Gram64, S64, Us64, Vs64, blk64
   add(householder_scratch_bytes(b));
+  add(small_svd_scratch_bytes(b));
   add(dgemm_scratch_bytes(b, b));
   return s + 8192;
 }
@@ -180,6 +182,7 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.Vs64 = (double*)ar.take((size_t)b * b * 8);
   w.blk64 = (double*)ar.take((size_t)b * b * 8);
   w.qr = (char*)ar.take(householder_scratch_bytes(b));
+  w.svd = (char*)ar.take(small_svd_scratch_bytes(b));
   w.dgemm_bytes = dgemm_scratch_bytes(b, b);
   w.dgemm = (double*)ar.take(w.dgemm_bytes);
   return w;
@@ -284,7 +287,8 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
   }
   // ---------------- small SVD (FP64) and fold-back (six-product BF16)
   RUTV_TRY(merge_f64(w.T, k, k, bi, bi, 0, w.blk64, bi, c.st));
-  RUTV_TRY(launch_small_svd((int)bi, w.blk64, bi, w.D, w.Us64, w.Vs64, c.status + 8, c.st));
+  RUTV_TRY(launch_small_svd((int)bi, w.blk64, bi, w.D, w.Us64, w.Vs64, c.status + 8, w.svd,
+                            w.dgemm, w.dgemm_bytes, c.st));
   RUTV_TRY(split_f64(w.Us64, bi, bi, bi, 0, w.Us, 0, 0, c.st));
   RUTV_TRY(split_f64(w.Vs64, bi, bi, bi, 0, w.Vs, 0, 0, c.st));
   if (k > 0) {  // T(0:k, blk) <- T(0:k, blk) Vs

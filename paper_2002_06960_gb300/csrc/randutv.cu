@@ -272,6 +272,7 @@ Plan make_plan(int64_t m, int64_t n, int64_t b) {
   add(small);  // Us
   add(small);  // Vs
   add(householder_scratch_bytes(b));
+  add(small_svd_scratch_bytes(b));
   add(dgemm_scratch_bytes(p.big, b));
   p.bytes = bytes + 4096;
   return p;
@@ -280,6 +281,7 @@ Plan make_plan(int64_t m, int64_t n, int64_t b) {
 struct Work {
   double *G, *Y, *Z, *W, *WS, *X, *tmp, *tau, *D, *Gm, *S, *Us, *Vs;
   char* qr;
+  char* svd;
   double* gemm;
   size_t gemm_bytes;
 };
@@ -302,6 +304,7 @@ Work carve(Arena& ar, const Plan& p) {
   w.Us = (double*)ar.take(small);
   w.Vs = (double*)ar.take(small);
   w.qr = (char*)ar.take(householder_scratch_bytes(p.b));
+  w.svd = (char*)ar.take(small_svd_scratch_bytes(p.b));
   w.gemm_bytes = dgemm_scratch_bytes(p.big, p.b);
   w.gemm = (double*)ar.take(w.gemm_bytes);
   return w;
@@ -379,7 +382,8 @@ int block_step(Ctx& c, int step, int64_t k, int64_t bi) {
     }
   }
   // ---- small SVD of the diagonal block and its fold-back
-  RUTV_TRY(launch_small_svd((int)bi, T22, ldt, w.D, w.Us, w.Vs, c.status + 8, c.st));
+  RUTV_TRY(launch_small_svd((int)bi, T22, ldt, w.D, w.Us, w.Vs, c.status + 8, w.svd, w.gemm,
+                            w.gemm_bytes, c.st));
   if (k > 0) {
     double* Tc = T + k * ldt;  // T(0:k, blk)
     RUTV_TRY(gemm(c, false, false, k, bi, bi, 1.0, Tc, ldt, w.Vs, bi, 0.0, w.tmp, k));
@@ -463,7 +467,7 @@ int randutv_profile_read(double* out, int nclass) {
 const char* randutv_profile_class_name(int cls) {
   static const char* names[K_NCLASS] = {"philox_normal", "dgemm", "householder_panel",
                                         "wy_factor", "jacobi_svd", "other", "bgemm_tcgen05",
-                                        "convert"};
+                                        "convert", "jacobi_svd_fp32"};
   return (cls >= 0 && cls < K_NCLASS) ? names[cls] : "?";
 }
 
@@ -656,7 +660,13 @@ int randutv_small_svd(int64_t b, const double* B, int64_t ldb, double* D, double
   if (!Vs) return -6;
   unsigned* status = nullptr;
   RUTV_TRY(status_words(&status));
-  return launch_small_svd((int)b, B, ldb, D, Us, Vs, status + 8, (cudaStream_t)stream);
+  const size_t sb = small_svd_scratch_bytes((int)b), gb = dgemm_scratch_bytes(b, b);
+  Arena ar;
+  RUTV_TRY(scratch_reserve(sb + gb + 1024, &ar));
+  void* svd = ar.take(sb);
+  double* gs = (double*)ar.take(gb);
+  return launch_small_svd((int)b, B, ldb, D, Us, Vs, status + 8, svd, gs, gb,
+                          (cudaStream_t)stream);
 }
 
 int randutv_dgemm(char transa, char transb, int64_t M, int64_t N, int64_t K, double alpha,
