@@ -51,6 +51,11 @@ def parse():
     ap.add_argument("--no-mixed", action="store_true",
                     help="skip the mixed-precision lines (16384^2 and 32768x8192, b=256, q=2)")
     ap.add_argument("--mixed-steps", type=int, default=3)
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched line (4096 matrices of sizes in [64, 1024])")
+    ap.add_argument("--batched-count", type=int, default=4096)
+    ap.add_argument("--no-backward", action="store_true",
+                    help="skip the rank-k backward line (4096^2, k=256, b=128)")
     return ap.parse_args()
 
 
@@ -392,6 +397,183 @@ def run_mixed(args, m, n, b, q, steps, warmup, fp64_ms=None):
     return out
 
 
+def _haar_gpu(n, p, g):
+    """n x p orthonormal columns (library QR of a seeded Gaussian; input preparation)."""
+    return torch.linalg.qr(torch.randn(n, p, generator=g, device="cuda", dtype=torch.float64))[0]
+
+
+def run_batched(args, count=4096, lo=64, hi=1024, q=1, steps=3, warmup=3):
+    """Batched form: `count` FP32 matrices, m and n i.i.d. uniform on [lo, hi],
+    A = Q1 diag(e^(-j/16)) Q2^T; block size per size class from the autotuner;
+    one persistent launch per step, replayed from a captured CUDA graph."""
+    import paper_2002_06960_gb300 as pkg
+    from paper_2002_06960_gb300 import batched
+
+    sizes = inputs.batch_sizes(count, lo, hi, seed=2)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2)
+    haar = {}
+
+    def factor(n):
+        if n not in haar:
+            haar[n] = _haar_gpu(n, n, g)
+        return haar[n]
+
+    As = []
+    for i, (m, n) in enumerate(sizes):
+        p = min(m, n)
+        sig = torch.exp(-torch.arange(p, dtype=torch.float64, device="cuda") / 16.0)
+        A = pkg.colmajor_empty(m, n, device="cuda", dtype=torch.float32)
+        A.copy_((factor(m)[:, :p] * sig) @ factor(n)[:, :p].T)
+        As.append(A)
+    haar.clear()
+
+    def make(m, n, i):
+        gg = torch.Generator(device="cuda")
+        gg.manual_seed(1000 + i)
+        p = min(m, n)
+        sig = torch.exp(-torch.arange(p, dtype=torch.float64, device="cuda") / 16.0)
+        A = pkg.colmajor_empty(m, n, device="cuda", dtype=torch.float32)
+        A.copy_((_haar_gpu(m, p, gg) * sig) @ _haar_gpu(n, p, gg).T)
+        return A
+
+    t0 = time.time()
+    tune = batched.autotune(make, per_class=24, q=q)
+    tune_s = time.time() - t0
+    plan = batched.BatchedPlan(As, b=0, q=q, seed=0)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan.run()
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        plan.run()
+    # graph.replay() launches on the current stream: replay and time on one stream
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            graph.replay()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(steps):
+            graph.replay()
+        e1.record(stream)
+    e1.synchronize()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    bad = int((plan.info != 0).sum())
+    b_of = {c: v[0] for c, v in tune.items()}
+    flops = sum(inputs.algorithmic_flops(m, n, b_of[batched.size_class(m, n)], q)
+                for (m, n) in sizes)
+    # errors of a sample of the matrices, in FP64 on the device
+    worst = {"recon": 0.0, "orth_u": 0.0, "orth_v": 0.0}
+    gs = torch.Generator().manual_seed(0)
+    for i in torch.randperm(count, generator=gs)[:16].tolist():
+        Ad = As[i].double()
+        U, T, V = plan.U[i].double(), plan.T[i].double(), plan.V[i].double()
+        worst["recon"] = max(worst["recon"], float(torch.linalg.norm(U @ T @ V.T - Ad) /
+                                                   torch.linalg.norm(Ad)))
+        for key, Q in (("orth_u", U), ("orth_v", V)):
+            e = Q.T @ Q - torch.eye(Q.shape[1], dtype=torch.float64, device="cuda")
+            worst[key] = max(worst[key], float(torch.linalg.norm(e) / Q.shape[1] ** 0.5))
+    sm_max = 2070.0
+    fp32_peak = dev_sms() * 128 * 2 * sm_max * 1e6 / 1e12
+    tf = flops / (ms * 1e-3) / 1e12
+    out = {
+        "workload": f"randutv_batched_{count}x_m_n_U[{lo},{hi}]_q{q}",
+        "value": round(count / (ms * 1e-3), 1), "unit": "matrices/s",
+        "tflops": round(tf, 3), "ms_per_step": round(ms, 2), "steps": steps, "warmup": warmup,
+        "dtype": "f32 (FFMA; FP64 Householder scalars; compensated FP32 Gram)",
+        "input": "Q1 diag(exp(-j/16)) Q2^T per matrix, FP32; sizes seeded (stream 5)",
+        "launch": "one persistent kernel per step, replayed from a CUDA graph",
+        "autotune": {str(c): {"b": v[0], "ms": round(v[1], 3)} for c, v in tune.items()},
+        "autotune_seconds": round(tune_s, 1),
+        "failed_matrices": bad,
+        "errors_worst_of_16": worst,
+        "roofline": {"bound": "alu", "kernel": "batched_kernel (FP32 FFMA)",
+                     "achieved": round(tf, 3), "peak": round(fp32_peak, 1), "unit": "TFLOP/s",
+                     "frac": round(tf / fp32_peak, 4),
+                     "peak_source": "152 SMs x 128 FFMA/clk x 2 flops x 2070 MHz (unit count x max clock)"},
+    }
+    plan.close()
+    del As, plan
+    torch.cuda.empty_cache()
+    return out
+
+
+def dev_sms():
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def run_backward(args, n=4096, k=256, b=128, q=1, steps=3, warmup=2, fp64_factor_ms=None):
+    """Backward form: gradient of L = ||A_k - B||_F^2 with A_k = U_k U_k^T A
+    through the first k/b randUTV steps (fixed sketch), A with the step
+    spectrum (gap at k), B i.i.d. N(0,1); forward and hand-written adjoint in
+    FP64.  The gradient is checked against central differences of the map."""
+    from paper_2002_06960_gb300 import autograd as ag
+
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    Q1 = _haar_gpu(n, n, g)
+    Q2 = _haar_gpu(n, n, g)
+    sig = inputs.spectrum("step", n, gap=k).cuda()
+    A = (Q1 * sig) @ Q2.T
+    del Q1, Q2
+    B = torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64)
+
+    def fwd_bwd():
+        X = A.clone().requires_grad_(True)
+        L = ((ag.lowrank(X, k, b, q, 0) - B) ** 2).sum()
+        L.backward()
+        return X.grad
+
+    for _ in range(warmup):
+        fwd_bwd()
+    torch.cuda.synchronize()
+    t_f, t_fb = [], []
+    for _ in range(steps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record()
+        X = A.clone().requires_grad_(True)
+        Ak = ag.lowrank(X, k, b, q, 0)
+        e1.record()
+        ((Ak - B) ** 2).sum().backward()
+        e2.record()
+        e2.synchronize()
+        t_f.append(e0.elapsed_time(e1))
+        t_fb.append(e0.elapsed_time(e2))
+    grad = X.grad
+    R = 2.0 * (Ak.detach() - B)
+    h = 1e-6 * float(A.norm())
+    errs = []
+    for _ in range(2):
+        E = torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64)
+        E /= E.norm()
+        with torch.no_grad():
+            dAk = (ag.lowrank(A + h * E, k, b, q, 0) - ag.lowrank(A - h * E, k, b, q, 0)) / (2 * h)
+        fd = float((R * dAk).sum())
+        an = float((grad * E).sum())
+        errs.append(abs(an - fd) / abs(fd))
+    ms_fb = statistics.median(t_fb)
+    out = {
+        "workload": f"randutv_lowrank_backward_n{n}_k{k}_b{b}_q{q}",
+        "value": round(ms_fb, 2), "unit": "ms per forward+backward", "higher_is_better": False,
+        "ms_forward": round(statistics.median(t_f), 2),
+        "ms_backward": round(ms_fb - statistics.median(t_f), 2),
+        "steps": steps, "warmup": warmup,
+        "dtype": "f64 (forward and hand-written adjoint)",
+        "input": "Q1 diag(step at k: 1 then 1e-6) Q2^T, B i.i.d. N(0,1)",
+        "gradient_rel_error_vs_central_differences": [float(f"{e:.3e}") for e in errs],
+    }
+    if fp64_factor_ms:
+        out["ratio_to_fp64_full_factorization_same_n"] = round(ms_fb / fp64_factor_ms, 4)
+    del A, B, grad, R
+    torch.cuda.empty_cache()
+    return out
+
+
 # ---------------------------------------------------------- oracle (CPU)
 
 def oracle_sample(n, b, q, seed, steps, A=None):
@@ -457,6 +639,17 @@ def main():
                 out["mixed"].append(run_mixed(args, 32768, 8192, 256, 2, 1, 3))
         except Exception as e:  # report, never hide
             out["mixed"] = {"error": repr(e)}
+    if world == 1 and not args.no_batched:
+        try:
+            out["batched"] = run_batched(args, count=args.batched_count)
+        except Exception as e:  # report, never hide
+            out["batched"] = {"error": repr(e)}
+    if world == 1 and not args.no_backward:
+        try:
+            out["backward"] = run_backward(
+                args, fp64_factor_ms=out["ms_per_step"] if args.n == 4096 else None)
+        except Exception as e:  # report, never hide
+            out["backward"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = oracle_sample(args.n, args.b, args.q, args.seed,

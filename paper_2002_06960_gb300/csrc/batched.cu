@@ -294,31 +294,27 @@ __device__ __forceinline__ void rr_pair_b(int round, int t, int P, int* p, int* 
   *q = a < c ? c : a;
 }
 
-// SVD of the bi x bi block B (column-major, ld ldb): D descending in sm.D,
-// Us, Vs (bi x bi, ld bi, global); signs as in the other paths.
-__device__ void cta_svd(int bi, const float* Bg, int64_t ldb, float* Us, float* Vs, Smem& sm) {
+// One-sided Jacobi sweeps on sm.svB (bi columns), rotations accumulated in
+// sm.svV, until a sweep rotates nothing or max_sweeps.
+//
+// The stopping threshold on |cos| is a few FP32 ulps, independent of bi: the
+// orthogonality of U_s = B V / D is that of the converged columns, and it
+// enters U and T at every fold-back.  Reaching it needs a_p.a_q without the
+// rounding noise of an FP32 dot product (about sqrt(bi) ulp of |a_p||a_q|,
+// which near convergence is far above a_p.a_q itself), so that one is a
+// compensated dot product.  Every lane of a group ends with bit-identical
+// sums, hence every row of the pair gets the same rotation.
+__device__ void cta_jacobi_sweeps(int bi, int max_sweeps, Smem& sm) {
   const int tid = threadIdx.x;
   const int P = (bi + 1) & ~1, npairs = P / 2;
-  for (int e = tid; e < P * BMAX; e += BT) {
-    const int j = e / BMAX, i = e % BMAX;
-    sm.svB[j][i] = (j < bi && i < bi) ? Bg[i + (int64_t)j * ldb] : 0.f;
-    sm.svV[j][i] = (j < bi && i < bi && i == j) ? 1.f : 0.f;
-  }
-  if (tid == 0) sm.flag = 0;
-  __syncthreads();
   int tpp = 1;
   while (tpp < 32 && tpp * 2 * npairs <= BT) tpp *= 2;
   const int g = tid / tpp, sub = tid % tpp;
   const bool active = g < npairs;
-  // The stopping threshold on |cos| is a few FP32 ulps, independent of bi: the
-  // orthogonality of U_s = B V / D is that of the converged columns, and it
-  // enters U and T at every fold-back.  Reaching it needs a_p.a_q without the
-  // rounding noise of an FP32 dot product (about sqrt(bi) ulp of |a_p||a_q|,
-  // which near convergence is far above a_p.a_q itself), so that one is a
-  // compensated dot product.  Every lane of a group ends with bit-identical
-  // sums, hence every row of the pair gets the same rotation.
   const float tol = 4.f * 0x1.0p-24f;
-  for (int sweep = 0; sweep < 30; ++sweep) {
+  if (tid == 0) sm.flag = 0;
+  __syncthreads();
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     for (int round = 0; round < P - 1; ++round) {
       int p = 0, q = 0;
       if (active) rr_pair_b(round, g, P, &p, &q);
@@ -347,7 +343,10 @@ __device__ void cta_svd(int bi, const float* Bg, int64_t ldb, float* Us, float* 
       if (active && q < bi && sc != 0.f && fabsf(sc) > tol * sqrtf(sa) * sqrtf(sb)) {
         const float zeta = (sb - sa) / (2.f * sc);
         const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
-        const float cs = rsqrtf(fmaf(t, t, 1.f)), sn = cs * t;
+        // correctly rounded: an approximate reciprocal square root leaves
+        // cs^2 + sn^2 off 1 by a few ulp with a bias, and thousands of
+        // rotations then drift the column norms of V (and of B, hence D)
+        const float cs = 1.f / sqrtf(fmaf(t, t, 1.f)), sn = cs * t;
         if (sub == 0) sm.flag = 1;
         for (int i = sub; i < bi; i += tpp) {
           const float x = sm.svB[p][i], y = sm.svB[q][i];
@@ -366,6 +365,81 @@ __device__ void cta_svd(int bi, const float* Bg, int64_t ldb, float* Us, float* 
     __syncthreads();
     if (!any) break;
   }
+}
+
+// SVD of the bi x bi block B (column-major, ld ldb): D descending in sm.D,
+// Us, Vs (bi x bi, ld bi, global); signs as in the other paths.
+//
+// FP32 sweeps to convergence leave two errors of the size of the rounding
+// accumulated over all the rotations (about sqrt(#rotations) ulp): V is
+// not quite orthogonal, and the rotated B is not quite B0 V.  Both are
+// removed by a refinement: V64 = V (3I - V^T V)/2 (one Newton-Schulz step,
+// Gram compensated, result held in FP64), B1 = B0 V64 (FP64 accumulation),
+// and FP32 sweeps on B1 from V = I, which are near-identity rotations with
+// correspondingly small rounding.  The output V is V64 V2.
+__device__ void cta_svd(int bi, const float* Bg, int64_t ldb, float* Us, float* Vs, Smem& sm) {
+  const int tid = threadIdx.x;
+  const int P = (bi + 1) & ~1;
+  for (int e = tid; e < P * BMAX; e += BT) {
+    const int j = e / BMAX, i = e % BMAX;
+    sm.svB[j][i] = (j < bi && i < bi) ? Bg[i + (int64_t)j * ldb] : 0.f;
+    sm.svV[j][i] = (j < bi && i < bi && i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  cta_jacobi_sweeps(bi, 30, sm);
+  // H' = -(V^T V - I) / 2 into svB (FP32: it is of the order of the rounding)
+  for (int e = tid; e < bi * bi; e += BT) {
+    const int i = e % bi, j = e / bi;
+    if (i > j) continue;
+    float sg = 0.f, cg = 0.f;
+    for (int k = 0; k < bi; ++k) {
+      const float x = sm.svV[i][k], y = sm.svV[j][k];
+      const float pr = x * y, pe = fmaf(x, y, -pr);
+      float t, te;
+      two_sum(sg, pr, t, te);
+      sg = t;
+      cg += te + pe;
+    }
+    const float h = -0.5f * (((i == j) ? sg - 1.f : sg) + cg);  // sg - 1 is exact
+    sm.svB[j][i] = h;
+    sm.svB[i][j] = h;
+  }
+  __syncthreads();
+  // V64 = V + V H' (FP64) into sm.S, S(i, j) at S[j][i]
+  for (int e = tid; e < bi * bi; e += BT) {
+    const int i = e % bi, j = e / bi;
+    double acc = 0.0;
+    for (int l = 0; l < bi; ++l) acc = fma((double)sm.svV[l][i], (double)sm.svB[j][l], acc);
+    sm.S[j][i] = (double)sm.svV[j][i] + acc;
+  }
+  __syncthreads();
+  // B1 = B0 V64 (FP64 accumulation), V2 = I
+  for (int e = tid; e < P * BMAX; e += BT) {
+    const int j = e / BMAX, i = e % BMAX;
+    float v = 0.f;
+    if (j < bi && i < bi) {
+      double acc = 0.0;
+      for (int l = 0; l < bi; ++l) acc = fma((double)Bg[i + (int64_t)l * ldb], sm.S[j][l], acc);
+      v = (float)acc;
+    }
+    sm.svB[j][i] = v;
+    sm.svV[j][i] = (j < bi && i < bi && i == j) ? 1.f : 0.f;
+  }
+  __syncthreads();
+  cta_jacobi_sweeps(bi, 10, sm);
+  // V = V64 V2 (FP64 accumulation) through Vs, then back into svV
+  for (int e = tid; e < bi * bi; e += BT) {
+    const int i = e % bi, j = e / bi;
+    double acc = 0.0;
+    for (int l = 0; l < bi; ++l) acc = fma(sm.S[l][i], (double)sm.svV[j][l], acc);
+    Vs[i + j * bi] = (float)acc;
+  }
+  __syncthreads();
+  for (int e = tid; e < bi * bi; e += BT) {
+    const int i = e % bi, j = e / bi;
+    sm.svV[j][i] = Vs[i + j * bi];
+  }
+  __syncthreads();
   // norms, order, signs
   if (tid < bi) {
     const int j = tid;

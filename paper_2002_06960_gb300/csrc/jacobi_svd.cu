@@ -45,7 +45,9 @@ namespace cg = cooperative_groups;
 namespace rutv {
 
 namespace {
-constexpr int SVD_THREADS = 256;
+constexpr int SVD_THREADS = 256;      // FP64 phase (few rows per CTA)
+constexpr int SVD_THREADS_FP32 = 512; // FP32 phase (one to four CTAs)
+constexpr int SVD_MAX_THREADS = 512;
 constexpr int SVD_MAX_B = 256;
 constexpr int SVD_DIRECT_B = 32;  // blocks up to this size skip the FP32 phase
 
@@ -74,14 +76,18 @@ size_t jac_smem_bytes(int b, int ncl) {
 __device__ __forceinline__ float fmar(float x, float y, float z) { return fmaf(x, y, z); }
 __device__ __forceinline__ double fmar(double x, double y, double z) { return fma(x, y, z); }
 
+// Pair t of round `round` of the circle ordering on P columns (0 <= t < P/2,
+// 0 <= round < P-1).
 __device__ __forceinline__ void rr_pair(int round, int t, int P, int* p, int* q) {
   int a, c;
   if (t == 0) {
     a = P - 1;
     c = round;
   } else {
-    a = (round + t) % (P - 1);
-    c = (round - t + (P - 1)) % (P - 1);
+    a = round + t;
+    if (a >= P - 1) a -= P - 1;
+    c = round - t;
+    if (c < 0) c += P - 1;
   }
   *p = a < c ? a : c;
   *q = a < c ? c : a;
@@ -92,13 +98,36 @@ __device__ double block_max(double v, double* red) {
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
   __syncthreads();
   double m = 0.0;
-  for (int w = 0; w < SVD_THREADS / 32; ++w) m = fmax(m, red[w]);
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
   __syncthreads();
   return m;
 }
 
+// Barrier across the cluster, or across the CTA when the cluster is one CTA.
+__device__ __forceinline__ void cluster_barrier(cg::cluster_group& cl, int ncl) {
+  if (ncl == 1) __syncthreads();
+  else cl.sync();
+}
+
+// Rotation angle of a pair (Rutishauser's formula), in the phase's precision.
+__device__ __forceinline__ void jac_rotation(double al, double be, double ga, double* c,
+                                             double* s) {
+  const double zeta = (be - al) / (2.0 * ga);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
+  *c = 1.0 / sqrt(fma(t, t, 1.0));
+  *s = *c * t;
+}
+__device__ __forceinline__ void jac_rotation(float al, float be, float ga, float* c, float* s) {
+  const float zeta = (be - al) / (2.f * ga);
+  const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
+  *c = 1.f / sqrtf(fmaf(t, t, 1.f));  // correctly rounded: no drift of the column norms
+  *s = *c * t;
+}
+__device__ __forceinline__ float sqrtr(float x) { return sqrtf(x); }
+__device__ __forceinline__ double sqrtr(double x) { return sqrt(x); }
+
 template <typename Real, bool kFinal>
-__global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
+__global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a) {
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
   const int ncl = (int)cl.num_blocks();
@@ -106,7 +135,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
   const int R = (b + ncl - 1) / ncl, LDR = R + 1;
   const int r0 = rank * R;
   const int nr = max(0, min(b, r0 + R) - r0);
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, nth = blockDim.x;
 
   extern __shared__ double smem[];
   double* npart = smem;               // [P] column norms^2 of own rows
@@ -120,14 +149,14 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
   int* vrow = reinterpret_cast<int*>(rot + (size_t)npairs * 2);
   int* rankof = vrow + P;
   __shared__ int s_rotated;
-  __shared__ double s_red[SVD_THREADS / 32];
+  __shared__ double s_red[SVD_MAX_THREADS / 32];
 
   // Phase 1 works on B 2^-e, e the exponent of max |B| (exact, and inside
   // the FP32 range whatever the scale of the block).
   double scale = 1.0;
   if (!kFinal) {
     double mx = 0.0;
-    for (int e = tid; e < b * b; e += SVD_THREADS)
+    for (int e = tid; e < b * b; e += nth)
       mx = fmax(mx, fabs(a.B[(e % b) + (int64_t)(e / b) * a.ldb]));
     mx = block_max(mx, s_red);
     if (mx > 0.0) {
@@ -136,7 +165,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
       scale = ldexp(1.0, -ex);
     }
   }
-  for (int e = tid; e < P * LDR; e += SVD_THREADS) {
+  for (int e = tid; e < P * LDR; e += nth) {
     const int j = e / LDR, i = e % LDR;
     const int gi = r0 + i;
     double bv = 0.0, vv = 0.0;
@@ -151,12 +180,12 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
   cl.sync();
 
   int tpp = 1;
-  while (tpp < 32 && tpp * 2 * npairs <= SVD_THREADS) tpp *= 2;
+  while (tpp < 32 && tpp * 2 * npairs <= nth) tpp *= 2;
   const int g = tid / tpp, sub = tid % tpp;
   const bool active = g < npairs;
   int NS = 1;
   while (NS < ncl) NS <<= 1;
-  const int ppc = (npairs + ncl - 1) / ncl;  // pairs owned per CTA; ppc * NS <= 2 npairs <= 256
+  const int ppc = (npairs + ncl - 1) / ncl;  // pairs owned per CTA; ppc * NS <= 2 npairs <= nth
   const int own_pl = tid / NS, own_src = tid % NS;
   const int own_pair = rank * ppc + own_pl;
   const bool own_lane = tid < ppc * NS && own_pair < npairs;
@@ -164,6 +193,61 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
 
   int sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
+    if (ncl == 1) {
+      // One CTA holds every row: each group reduces its pair's sums by
+      // shuffles (bit-identical in all its lanes), takes the rotation and
+      // applies it; one block barrier per round.
+      for (int round = 0; round < P - 1; ++round) {
+        int p = 0, q = 0;
+        Real sa = 0, sb = 0, sc = 0;
+        if (active) {
+          rr_pair(round, g, P, &p, &q);
+          const Real* bp = Bl + (size_t)p * LDR;
+          const Real* bq = Bl + (size_t)q * LDR;
+#pragma unroll 4
+          for (int i = sub; i < nr; i += tpp) {
+            const Real x = bp[i], y = bq[i];
+            sa = fmar(x, x, sa);
+            sb = fmar(y, y, sb);
+            sc = fmar(x, y, sc);
+          }
+        }
+        // every thread shuffles (inactive ones carry zeros): a warp may hold
+        // active and inactive groups
+        for (int o = tpp >> 1; o > 0; o >>= 1) {
+          sa += __shfl_xor_sync(0xffffffffu, sa, o);
+          sb += __shfl_xor_sync(0xffffffffu, sb, o);
+          sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        }
+        if (active) {
+          Real* bp = Bl + (size_t)p * LDR;
+          Real* bq = Bl + (size_t)q * LDR;
+          if (q < b && sc != (Real)0 && fabs(sc) > (Real)tol * sqrtr(sa) * sqrtr(sb)) {
+            Real c, s;
+            jac_rotation(sa, sb, sc, &c, &s);
+            if (sub == 0) s_rotated = 1;
+            Real* vp = Vl + (size_t)p * LDR;
+            Real* vq = Vl + (size_t)q * LDR;
+#pragma unroll 4
+            for (int i = sub; i < nr; i += tpp) {
+              const Real x = bp[i], y = bq[i];
+              bp[i] = fmar(c, x, -s * y);
+              bq[i] = fmar(s, x, c * y);
+              const Real u = vp[i], w = vq[i];
+              vp[i] = fmar(c, u, -s * w);
+              vq[i] = fmar(s, u, c * w);
+            }
+          }
+        }
+        __syncthreads();
+      }
+      const int any = s_rotated;
+      __syncthreads();
+      if (tid == 0) s_rotated = 0;
+      __syncthreads();
+      if (!any) break;
+      continue;
+    }
     for (int round = 0; round < P - 1; ++round) {
       int p = 0, q = 0;
       if (active) rr_pair(round, g, P, &p, &q);
@@ -189,13 +273,14 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
         part[(size_t)g * 3 + 1] = sb;
         part[(size_t)g * 3 + 2] = sc;
       }
-      cl.sync();
+      cluster_barrier(cl, ncl);
       // owned pairs: sum the partials of all CTAs (fixed shuffle tree, so every
       // lane of the group ends with the same sums) and broadcast the rotation
       {
         double al = 0.0, be = 0.0, ga = 0.0;
         if (own_lane && own_src < ncl) {
-          const Real* rp = cl.map_shared_rank(part, own_src) + (size_t)own_pair * 3;
+          const Real* rp =
+              (ncl == 1 ? part : cl.map_shared_rank(part, own_src)) + (size_t)own_pair * 3;
           al = (double)rp[0];
           be = (double)rp[1];
           ga = (double)rp[2];
@@ -205,25 +290,21 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
           be += __shfl_xor_sync(0xffffffffu, be, o);
           ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        double c = 1.0, s = 0.0;
+        Real c = 1, s = 0;
         if (own_lane) {
           int pp, qq;
           rr_pair(round, own_pair, P, &pp, &qq);
-          if (qq < b && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be)) {
-            const double zeta = (be - al) / (2.0 * ga);
-            const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + hypot(1.0, zeta));
-            c = 1.0 / sqrt(fma(t, t, 1.0));
-            s = c * t;
-          }
+          if (qq < b && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be))
+            jac_rotation((Real)al, (Real)be, (Real)ga, &c, &s);
         }
         if (own_lane && own_src < ncl) {
-          Real* rr = cl.map_shared_rank(rot, own_src) + (size_t)own_pair * 2;
-          rr[0] = (Real)c;
-          rr[1] = (Real)s;
-          if (own_src == 0 && s != 0.0) s_rotated = 1;
+          Real* rr = (ncl == 1 ? rot : cl.map_shared_rank(rot, own_src)) + (size_t)own_pair * 2;
+          rr[0] = c;
+          rr[1] = s;
+          if (own_src == 0 && s != (Real)0) s_rotated = 1;
         }
       }
-      cl.sync();
+      cluster_barrier(cl, ncl);
       if (active) {
         const Real c = rot[(size_t)g * 2], s = rot[(size_t)g * 2 + 1];
         if (s != (Real)0) {
@@ -255,7 +336,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
 
   if (!kFinal) {
     if (rank == 0 && tid == 0 && a.info) a.info[0] = (unsigned)sweep;
-    for (int e = tid; e < b * nr; e += SVD_THREADS) {
+    for (int e = tid; e < b * nr; e += nth) {
       const int j = e / nr, i = e % nr;
       a.V32[(r0 + i) + (int64_t)j * b] = (float)Vl[(size_t)j * LDR + i];
     }
@@ -263,7 +344,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
   }
 
   // column norms and the signed entry of largest |V| per column (own rows)
-  for (int j = tid; j < P; j += SVD_THREADS) {
+  for (int j = tid; j < P; j += nth) {
     double s2 = 0.0, bestabs = -1.0;
     int bi = 0;
     for (int i = 0; i < nr; ++i) {
@@ -280,7 +361,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
     vrow[j] = r0 + bi;
   }
   cl.sync();
-  for (int j = tid; j < P; j += SVD_THREADS) {
+  for (int j = tid; j < P; j += nth) {
     // The running maximum keeps its magnitude and its owner explicitly; the
     // signed value is fetched from the owning CTA once the winner is known.
     double s2 = 0.0, bestabs = -1.0;
@@ -297,7 +378,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
     vbest[j] = cl.map_shared_rank(vmax, bestk)[j];
   }
   cl.sync();  // every CTA has finished reading the others' vmax/npart
-  for (int j = tid; j < b; j += SVD_THREADS) {
+  for (int j = tid; j < b; j += nth) {
     const double dj = Dfull[j];
     int rk = 0;
     for (int l = 0; l < b; ++l) {
@@ -308,7 +389,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
   }
   __syncthreads();
   // write outputs: column j goes to position rankof[j]
-  for (int e = tid; e < b * nr; e += SVD_THREADS) {
+  for (int e = tid; e < b * nr; e += nth) {
     const int j = e / nr, i = e % nr;
     const int pos = rankof[j];
     const double sg = (vbest[j] < 0.0) ? -1.0 : 1.0;
@@ -318,7 +399,7 @@ __global__ void __launch_bounds__(SVD_THREADS) jacobi_kernel(const JacArgs a) {
     a.Us[gi + (int64_t)pos * b] = (dj > 0.0) ? sg * ((double)Bl[(size_t)j * LDR + i] / dj) : 0.0;
   }
   if (rank == 0) {
-    for (int j = tid; j < b; j += SVD_THREADS) a.D[rankof[j]] = Dfull[j];
+    for (int j = tid; j < b; j += nth) a.D[rankof[j]] = Dfull[j];
     if (tid == 0 && a.info) a.info[0] = (unsigned)sweep;
   }
 }
@@ -403,7 +484,7 @@ int launch_jacobi(const JacArgs& a, int ncl, cudaStream_t st) {
   at[0].val.clusterDim.y = 1;
   at[0].val.clusterDim.z = 1;
   cfg.gridDim = dim3((unsigned)ncl);
-  cfg.blockDim = dim3(SVD_THREADS);
+  cfg.blockDim = dim3(kFinal ? SVD_THREADS : SVD_THREADS_FP32);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cfg.attrs = at;
