@@ -211,7 +211,7 @@ int randutv_householder_qr(int64_t r, int64_t c, double* panel, int64_t ld, doub
  * real-time loops that cannot afford an allocation's latency or failure.
  * This entry point serves them: it calls no cudaMalloc, cudaFree or other
  * allocating routine.  Its scratch is a fixed array inside the library
- * (about 386 KiB: partial sums for up to 192 SMs x 256 columns, plus its
+ * (about 388 KiB: partial sums for up to 192 SMs x 256 columns, plus its
  * barrier and status words), which every GPU that loads the library holds
  * until the process exits.
  *   Arguments, layout and results are those of randutv_householder_qr; the
@@ -230,7 +230,7 @@ int randutv_householder_qr_noalloc(int64_t r, int64_t c, double* panel, int64_t 
 
 /* Compact-WY factor (Fig. 2: T_V, T_U): S (c x c, ld c, upper triangular)
  * with H_1 ... H_c = I - W S W^T, for W (r x c, ld r) and tau from
- * randutv_householder_qr. */
+ * randutv_householder_qr; 1 <= c <= min(r, 256). */
 int randutv_wy_factor(int64_t r, int64_t c, const double* W, const double* tau, double* S,
                       void* stream);
 

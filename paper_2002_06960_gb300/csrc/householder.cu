@@ -7,20 +7,30 @@
 //
 // The panel has r rows (up to the matrix height) and c <= 256 columns, so
 // the reflector of each column needs a reduction over all r rows.  One
-// cooperative grid (one CTA per SM at most) walks the columns: each CTA owns
-// a contiguous slice of rows, and two bounded grid barriers per column
-// separate (1) the partial squared norms below the diagonal, (2) the partial
-// dot products of the reflector with the trailing columns, and (3) the rank-1
-// update.  Every cross-CTA sum is taken in CTA order, so the result is
-// bitwise reproducible.  Values written by another CTA (the partial sums and
-// the diagonal entry) are read with L2-only loads: L1 is not coherent
-// across SMs.
+// cooperative grid (one CTA per SM at most) walks the columns; each CTA owns
+// a contiguous slice of rows, held in shared memory when it fits (it does for
+// 16384 x 256 on 152 SMs), else read and written in place through L2.  Three
+// bounded grid barriers per column separate
+//   (1) the partial squared norms below the diagonal (and the diagonal entry,
+//       published by the CTA that owns it),
+//   (2) the reflector, identical in every CTA, and the partial dot products
+//       of the reflector with the trailing columns,
+//   (2') the sums of those partials: the CTA k owns the trailing columns
+//       l = j + 1 + k (mod CTAs) and publishes tau * sum,
+//   (3) the rank-1 update of every CTA's rows with the published sums.
+// Summing each column's partials once (2') instead of in every CTA keeps the
+// traffic per column at O(CTAs * c) rather than O(CTAs^2 * c).  Every
+// cross-CTA sum is taken in a fixed order, so the result is bitwise
+// reproducible.  Values written by another CTA are read with L2-only loads:
+// L1 is not coherent across SMs.
 #include "common.cuh"
 
 namespace rutv {
 
 namespace {
 constexpr int QR_THREADS = 256;
+constexpr int QR_WARPS = QR_THREADS / 32;
+constexpr size_t kQrSmemMax = 220 * 1024;  // own rows kept in shared memory up to this size
 
 struct QrArgs {
   int64_t r, c;
@@ -28,37 +38,53 @@ struct QrArgs {
   int64_t lda;
   double* W;       // r x c, ld r
   double* tau;     // c
-  double* part1;   // nblocks
-  double* part2;   // nblocks x c
+  double* part1;   // nblocks + 1: partial norms, then the diagonal entry of the column
+  double* part2;   // nblocks x c: partial dot products
+  double* tot;     // c: tau * sum of the partial dot products (one writer per column)
   unsigned* bar;   // {count, generation}
   unsigned* err;
 };
 
+template <bool kSmem>
 __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a) {
-  __shared__ double red[QR_THREADS / 32];
-  __shared__ double s_coef[4];  // tau, scale, beta, (unused)
+  extern __shared__ double smA[];  // kSmem: own rows, column-major, ld rows_per
+  __shared__ double red[QR_WARPS];
+  __shared__ double s_coef[4];  // tau, scale, beta
   const unsigned nb = gridDim.x;
   const int64_t rows_per = (a.r + nb - 1) / nb;
   const int64_t i0 = (int64_t)blockIdx.x * rows_per;
   const int64_t i1 = (i0 + rows_per < a.r) ? i0 + rows_per : a.r;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = QR_THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // element (i, l) of the panel, i in [i0, i1)
+  auto at = [&](int64_t i, int64_t l) -> double& {
+    if (kSmem) return smA[(i - i0) + l * rows_per];
+    return a.A[i + l * a.lda];
+  };
+  if (kSmem) {
+    for (int64_t l = 0; l < a.c; ++l)
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += QR_THREADS) at(i, l) = a.A[i + l * a.lda];
+    __syncthreads();
+  }
 
   // W starts as zero above the diagonal; column j is written in step 3 of j.
   for (int64_t j = 0; j < a.c; ++j) {
-    // ---- phase 1: partial sum of squares of A(j+1:r, j) over own rows
+    // ---- (1) partial sum of squares of A(j+1:r, j) over own rows
     double ss = 0.0;
     {
       const int64_t lo = (i0 > j + 1) ? i0 : j + 1;
       for (int64_t i = lo + threadIdx.x; i < i1; i += QR_THREADS) {
-        const double x = a.A[i + j * a.lda];
+        const double x = at(i, j);
         ss = fma(x, x, ss);
       }
     }
     ss = block_sum(ss, red);
-    if (threadIdx.x == 0) a.part1[blockIdx.x] = ss;
+    if (threadIdx.x == 0) {
+      a.part1[blockIdx.x] = ss;
+      if (j >= i0 && j < i1) a.part1[nb] = at(j, j);
+    }
     if (!grid_barrier(a.bar, nb, a.err, 1)) return;
 
-    // ---- phase 2: reflector scalars (every CTA, same order), partial dots
+    // ---- (2) reflector scalars (every CTA, same order), partial dots
     if (warp == 0) {
       // lanes load the partials in parallel; the fixed shuffle tree makes the
       // sum identical in every CTA
@@ -66,68 +92,72 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
       for (unsigned t = lane; t < nb; t += 32) sig2 += __ldcg(a.part1 + t);
       for (int o = 16; o > 0; o >>= 1) sig2 += __shfl_xor_sync(0xffffffffu, sig2, o);
       if (lane == 0) {
-      const double alpha = __ldcg(a.A + j + j * a.lda);  // row j may be another CTA's
-      double tau, scale, beta;
-      if (sig2 == 0.0) {
-        tau = 0.0; beta = alpha; scale = 0.0;
-      } else {
-        const double nrm = sqrt(fma(alpha, alpha, sig2));
-        beta = (alpha >= 0.0) ? -nrm : nrm;
-        tau = (beta - alpha) / beta;
-        scale = 1.0 / (alpha - beta);
-      }
-      s_coef[0] = tau; s_coef[1] = scale; s_coef[2] = beta;
+        const double alpha = __ldcg(a.part1 + nb);
+        double tau, scale, beta;
+        if (sig2 == 0.0) {
+          tau = 0.0; beta = alpha; scale = 0.0;
+        } else {
+          const double nrm = sqrt(fma(alpha, alpha, sig2));
+          beta = (alpha >= 0.0) ? -nrm : nrm;
+          tau = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        s_coef[0] = tau; s_coef[1] = scale; s_coef[2] = beta;
       }
     }
     __syncthreads();
     const double tau = s_coef[0], scale = s_coef[1];
     // dot_l = sum_{i >= j} v_i A(i, l) for l > j, v_j = 1, v_i = A(i,j) * scale
-    // Each warp takes its columns l = j+1+warp+nwarp*t in groups of 8 and
+    // Each warp takes its columns l = j+1+warp+QR_WARPS*t in groups of 8 and
     // walks its rows once per group, so the loads of a row are independent
     // and in flight together.
     const int64_t lo = (i0 > j) ? i0 : j;
-    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)nwarp) {
+    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
       double d[8];
 #pragma unroll
       for (int t = 0; t < 8; ++t) d[t] = 0.0;
       for (int64_t i = lo + lane; i < i1; i += 32) {
-        const double v = (i == j) ? 1.0 : a.A[i + j * a.lda] * scale;
+        const double v = (i == j) ? 1.0 : at(i, j) * scale;
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
-          const int64_t l = l0 + (int64_t)t * nwarp;
-          if (l < a.c) d[t] = fma(v, a.A[i + l * a.lda], d[t]);
+          const int64_t l = l0 + (int64_t)t * QR_WARPS;
+          if (l < a.c) d[t] = fma(v, at(i, l), d[t]);
         }
       }
 #pragma unroll
       for (int t = 0; t < 8; ++t) {
         double x = d[t];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        const int64_t l = l0 + (int64_t)t * nwarp;
+        const int64_t l = l0 + (int64_t)t * QR_WARPS;
         if (lane == 0 && l < a.c) a.part2[(int64_t)blockIdx.x * a.c + l] = x;
       }
     }
     if (!grid_barrier(a.bar, nb, a.err, 2)) return;
 
-    // ---- phase 3: rank-1 update of own rows, write W(:, j), R(j, j), zeros
-    // w_l = tau * sum_t part2[t][l]  (each warp sums the columns it updates)
-    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)nwarp) {
-      double w[8];
+    // ---- (2') sums of the partials of the columns this CTA owns
+    for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * warp; l < a.c; l += (int64_t)nb * QR_WARPS) {
+      double s = 0.0;
+      for (unsigned u = lane; u < nb; u += 32) s += __ldcg(a.part2 + (int64_t)u * a.c + l);
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0) a.tot[l] = s * tau;
+    }
+    if (!grid_barrier(a.bar, nb, a.err, 3)) return;
+
+    // ---- (3) rank-1 update of own rows, write W(:, j), R(j, j), zeros
+    if (tau != 0.0) {
+      for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
+        double w[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        const int64_t l = l0 + (int64_t)t * nwarp;
-        double s = 0.0;
-        if (l < a.c)
-          for (unsigned u = lane; u < nb; u += 32) s += __ldcg(a.part2 + (int64_t)u * a.c + l);
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        w[t] = s * tau;
-      }
-      if (tau != 0.0) {
+        for (int t = 0; t < 8; ++t) {
+          const int64_t l = l0 + (int64_t)t * QR_WARPS;
+          w[t] = (l < a.c) ? __ldcg(a.tot + l) : 0.0;
+        }
         for (int64_t i = lo + lane; i < i1; i += 32) {
-          const double v = (i == j) ? 1.0 : a.A[i + j * a.lda] * scale;
+          const double v = (i == j) ? 1.0 : at(i, j) * scale;
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
-            const int64_t l = l0 + (int64_t)t * nwarp;
-            if (l < a.c) a.A[i + l * a.lda] = fma(-v, w[t], a.A[i + l * a.lda]);
+            const int64_t l = l0 + (int64_t)t * QR_WARPS;
+            if (l < a.c) at(i, l) = fma(-v, w[t], at(i, l));
           }
         }
       }
@@ -137,67 +167,134 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
       double wv;
       if (i < j) wv = 0.0;
       else if (i == j) wv = 1.0;
-      else wv = (tau != 0.0) ? a.A[i + j * a.lda] * scale : 0.0;
+      else wv = (tau != 0.0) ? at(i, j) * scale : 0.0;
       a.W[i + j * a.r] = wv;
-      if (i > j) a.A[i + j * a.lda] = 0.0;
-      if (i == j) a.A[i + j * a.lda] = s_coef[2];
+      if (i > j) at(i, j) = 0.0;
+      if (i == j) at(i, j) = s_coef[2];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.tau[j] = tau;
     __syncthreads();
   }
+  if (kSmem) {
+    for (int64_t l = 0; l < a.c; ++l)
+      for (int64_t i = i0 + threadIdx.x; i < i1; i += QR_THREADS) a.A[i + l * a.lda] = at(i, l);
+  }
 }
 
-// S (c x c, ld c) from the Gram matrix Gm = W^T W (c x c, ld c) and tau:
-// S_jj = tau_j, S(0:j, j) = -tau_j S(0:j, 0:j) Gm(0:j, j).  One CTA.
-__global__ void wy_factor_kernel(int64_t c, const double* __restrict__ Gm,
-                                 const double* __restrict__ tau, double* __restrict__ S) {
-  for (int64_t e = threadIdx.x; e < c * c; e += blockDim.x) S[e] = 0.0;
-  __syncthreads();
-  for (int64_t j = 0; j < c; ++j) {
-    const double tj = tau[j];
-    for (int64_t i = threadIdx.x; i < j; i += blockDim.x) {
-      double s = 0.0;
-      for (int64_t l = i; l < j; ++l) s = fma(S[i + l * c], Gm[l + j * c], s);
-      S[i + j * c] = -tj * s;
+// Number of CTAs of the panel kernel: at least 64 rows each, at most one per SM.
+int qr_blocks(int64_t r) {
+  const int sms = dev_info().sms;
+  int nb = (int)((r + 63) / 64);
+  if (nb > sms) nb = sms;
+  if (nb < 1) nb = 1;
+  return nb;
+}
+
+// Scratch layout: part1 (SMs + 1), part2 (SMs x c), tot (c), in doubles.
+void qr_carve(QrArgs& a, double* base, int sms) {
+  a.part1 = base;
+  a.part2 = a.part1 + sms + 1;
+  a.tot = a.part2 + (size_t)sms * a.c;
+}
+
+int qr_launch(QrArgs& a, int nb, cudaStream_t st) {
+  const int64_t rows_per = (a.r + nb - 1) / nb;
+  const size_t smem = (size_t)rows_per * (size_t)a.c * sizeof(double);
+  void* args[] = {&a};
+  if (smem <= kQrSmemMax) {
+    static bool configured = false;
+    if (!configured) {
+      RUTV_CK(cudaFuncSetAttribute(householder_panel_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemMax));
+      configured = true;
     }
-    if (threadIdx.x == 0) S[j + j * c] = tj;
-    __syncthreads();
+    RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel<true>, dim3(nb),
+                                        dim3(QR_THREADS), args, smem, st));
+  } else {
+    RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel<false>, dim3(nb),
+                                        dim3(QR_THREADS), args, 0, st));
   }
+  note_launch();
+  return 0;
+}
+
+// S (c x c, ld c) from the Gram matrix Gm = W^T W (c x c, ld c) and tau, the
+// compact-WY factor of H_1 ... H_c = I - W S W^T (forward, column-wise):
+// S_jj = tau_j, S(0:j, j) = -tau_j S(0:j, 0:j) Gm(0:j, j).
+// That recurrence is the inverse of the upper triangle striu(Gm) + diag(1/tau)
+// (for tau_j != 0), so every column of S is a back substitution of its own:
+//   S(i, k) = tau_i (delta_ik - sum_{l=i+1..k} Gm(i, l) S(l, k)),  i = k..0,
+// which also gives the zero rows and columns of reflectors with tau = 0.
+// One warp per column k, S(:, k) in shared memory; Gm(i, l) is read as
+// Gm(l, i) (Gm is symmetric) so that the lanes read contiguous memory, and
+// the next row's operands are loaded while the current row is reduced.
+constexpr int WY_WARPS = 8;
+constexpr int WY_MAXC = 256;
+
+__global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const double* __restrict__ Gm,
+                                                                   const double* __restrict__ tau,
+                                                                   double* __restrict__ S) {
+  __shared__ double col[WY_WARPS][WY_MAXC];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * WY_WARPS + warp;
+  if (k >= c) return;  // whole warps leave; no block barrier below
+  double* sk = col[warp];
+  constexpr int NL = WY_MAXC / 32;  // operands per lane per row
+  double gcur[NL], gnext[NL];
+  // operands of row i: Gm(l, i) for l = i+1+lane+32t <= k
+  auto load_row = [&](int i, double* g) {
+#pragma unroll
+    for (int t = 0; t < NL; ++t) {
+      const int l = i + 1 + lane + 32 * t;
+      g[t] = (i >= 0 && l <= k) ? Gm[l + (int64_t)i * c] : 0.0;
+    }
+  };
+  load_row(k, gcur);
+  double tcur = tau[k];
+  for (int i = k; i >= 0; --i) {
+    load_row(i - 1, gnext);
+    const double tnext = (i > 0) ? tau[i - 1] : 0.0;
+    double acc = 0.0;
+#pragma unroll
+    for (int t = 0; t < NL; ++t) {
+      const int l = i + 1 + lane + 32 * t;
+      if (l <= k) acc = fma(gcur[t], sk[l], acc);
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) sk[i] = tcur * (((i == k) ? 1.0 : 0.0) - acc);
+    __syncwarp();
+#pragma unroll
+    for (int t = 0; t < NL; ++t) gcur[t] = gnext[t];
+    tcur = tnext;
+  }
+  for (int i = lane; i < c; i += 32) S[i + (int64_t)k * c] = (i <= k) ? sk[i] : 0.0;
 }
 }  // namespace
 
 size_t householder_scratch_bytes(int64_t c) {
   const int nb = dev_info().sms;
-  return (size_t)nb * sizeof(double) + (size_t)nb * (size_t)c * sizeof(double) + 512;
+  return ((size_t)nb + 1 + (size_t)nb * (size_t)c + (size_t)c) * sizeof(double) + 512;
 }
 
 int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* W, double* tau,
                           char* scratch, unsigned* bar, unsigned* err, cudaStream_t st) {
   if (c <= 0) return 0;
-  const int sms = dev_info().sms;
-  int nb = (int)((r + 63) / 64);  // at least 64 rows per CTA
-  if (nb > sms) nb = sms;
-  if (nb < 1) nb = 1;
+  const int nb = qr_blocks(r);
   QrArgs a;
   a.r = r; a.c = c; a.A = A; a.lda = lda; a.W = W; a.tau = tau;
-  a.part1 = (double*)scratch;
-  a.part2 = a.part1 + sms;
+  qr_carve(a, (double*)scratch, dev_info().sms);
   a.bar = bar; a.err = err;
   ProfScope prof(K_QR, 2.0 * (double)c * c * ((double)r - c / 3.0), 24.0 * (double)r * c, st);
   RUTV_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
-  void* args[] = {&a};
-  RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel, dim3(nb),
-                                      dim3(QR_THREADS), args, 0, st));
-  note_launch();
-  return 0;
+  return qr_launch(a, nb, st);
 }
 
 int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st) {
   if (c <= 0) return 0;
-  int threads = (int)((c + 31) / 32 * 32);
-  if (threads > 256) threads = 256;
+  if (c > WY_MAXC) return RANDUTV_EUNSUPPORTED;
   ProfScope prof(K_WY, (double)c * c * c / 3.0, 16.0 * (double)c * c, st);
-  wy_factor_kernel<<<1, threads, 0, st>>>(c, Gm, tau, S);
+  wy_factor_kernel<<<(unsigned)((c + WY_WARPS - 1) / WY_WARPS), WY_WARPS * 32, 0, st>>>((int)c, Gm,
+                                                                                        tau, S);
   note_launch();
   RUTV_CK(cudaGetLastError());
   return 0;
@@ -213,7 +310,7 @@ int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, 
 // library normally takes these from its own growing scratch, which it
 // allocates with cudaMalloc on first use.  This variant keeps them in one
 // fixed array in the library's device image instead, sized for at most
-// kNoAllocMaxSms SMs and kNoAllocMaxCols columns (about 386 KiB).  Every GPU
+// kNoAllocMaxSms SMs and kNoAllocMaxCols columns (about 388 KiB).  Every GPU
 // that loads the library holds that array until the process exits.
 #include <mutex>
 
@@ -222,7 +319,8 @@ namespace {
 
 constexpr int kNoAllocMaxSms = 192;
 constexpr int kNoAllocMaxCols = 256;
-constexpr size_t kNoAllocPartials = (size_t)kNoAllocMaxSms * (1 + kNoAllocMaxCols);
+constexpr size_t kNoAllocPartials =
+    (size_t)kNoAllocMaxSms * (1 + kNoAllocMaxCols) + 1 + kNoAllocMaxCols;
 constexpr size_t kNoAllocBytes = kNoAllocPartials * sizeof(double) + 256;
 
 // Partials first, then 64 status words: [0] error, [1] site, [2..3] barrier.
@@ -276,18 +374,13 @@ extern "C" int randutv_householder_qr_noalloc(int64_t r, int64_t c, double* pane
   // error, site and barrier words start at zero; the partials are always
   // written before they are read
   RUTV_CK(cudaMemsetAsync(words, 0, 4 * sizeof(unsigned), st));
-  int nb = (int)((r + 63) / 64);
-  if (nb > sms) nb = sms;
+  const int nb = qr_blocks(r);
   QrArgs a;
   a.r = r; a.c = c; a.A = panel; a.lda = ld; a.W = W; a.tau = tau;
-  a.part1 = (double*)base;
-  a.part2 = a.part1 + sms;
+  qr_carve(a, (double*)base, sms);
   a.bar = words + 2;
   a.err = words;
-  void* args[] = {&a};
-  RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel, dim3(nb),
-                                      dim3(QR_THREADS), args, 0, st));
-  note_launch();
+  RUTV_TRY(qr_launch(a, nb, st));
   unsigned h[2] = {0, 0};
   RUTV_CK(cudaMemcpyAsync(h, words, sizeof h, cudaMemcpyDeviceToHost, st));
   RUTV_CK(cudaStreamSynchronize(st));

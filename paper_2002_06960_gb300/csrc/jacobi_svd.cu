@@ -179,10 +179,21 @@ __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a
   if (tid == 0) s_rotated = 0;
   cl.sync();
 
+  // Lanes per pair: a group of tpp consecutive lanes covers consecutive rows
+  // of one column, and each group walks the pairs g = group, group + ngroups,
+  // ...  (the trip count is the same for every group, so the shuffles run in
+  // whole warps).  One CTA with many rows per pair: tpp = min(32, R), which
+  // keeps a warp's shared-memory accesses conflict-free.  A cluster, with few
+  // rows per CTA: as many pairs in flight as the block allows, so that a
+  // round is one short pass rather than a chain of reductions.
   int tpp = 1;
-  while (tpp < 32 && tpp * 2 * npairs <= nth) tpp *= 2;
-  const int g = tid / tpp, sub = tid % tpp;
-  const bool active = g < npairs;
+  if (ncl == 1) {
+    while (tpp < 32 && tpp < R) tpp *= 2;
+  } else {
+    while (tpp < 32 && tpp * 2 * npairs <= nth) tpp *= 2;
+  }
+  const int group = tid / tpp, sub = tid % tpp, ngroups = nth / tpp;
+  const int pair_iters = (npairs + ngroups - 1) / ngroups;
   int NS = 1;
   while (NS < ncl) NS <<= 1;
   const int ppc = (npairs + ncl - 1) / ncl;  // pairs owned per CTA; ppc * NS <= 2 npairs <= nth
@@ -190,6 +201,7 @@ __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a
   const int own_pair = rank * ppc + own_pl;
   const bool own_lane = tid < ppc * NS && own_pair < npairs;
   const double tol = a.tol;
+  const Real tol_r = (Real)tol;
 
   int sweep = 0;
   for (; sweep < a.max_sweeps; ++sweep) {
@@ -198,34 +210,34 @@ __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a
       // shuffles (bit-identical in all its lanes), takes the rotation and
       // applies it; one block barrier per round.
       for (int round = 0; round < P - 1; ++round) {
-        int p = 0, q = 0;
-        Real sa = 0, sb = 0, sc = 0;
-        if (active) {
-          rr_pair(round, g, P, &p, &q);
-          const Real* bp = Bl + (size_t)p * LDR;
-          const Real* bq = Bl + (size_t)q * LDR;
+        for (int it = 0; it < pair_iters; ++it) {
+          const int g = group + it * ngroups;
+          const bool act = g < npairs;
+          int p = 0, q = 0;
+          Real sa = 0, sb = 0, sc = 0;
+          if (act) {
+            rr_pair(round, g, P, &p, &q);
+            const Real* bp = Bl + (size_t)p * LDR;
+            const Real* bq = Bl + (size_t)q * LDR;
 #pragma unroll 4
-          for (int i = sub; i < nr; i += tpp) {
-            const Real x = bp[i], y = bq[i];
-            sa = fmar(x, x, sa);
-            sb = fmar(y, y, sb);
-            sc = fmar(x, y, sc);
+            for (int i = sub; i < nr; i += tpp) {
+              const Real x = bp[i], y = bq[i];
+              sa = fmar(x, x, sa);
+              sb = fmar(y, y, sb);
+              sc = fmar(x, y, sc);
+            }
           }
-        }
-        // every thread shuffles (inactive ones carry zeros): a warp may hold
-        // active and inactive groups
-        for (int o = tpp >> 1; o > 0; o >>= 1) {
-          sa += __shfl_xor_sync(0xffffffffu, sa, o);
-          sb += __shfl_xor_sync(0xffffffffu, sb, o);
-          sc += __shfl_xor_sync(0xffffffffu, sc, o);
-        }
-        if (active) {
-          Real* bp = Bl + (size_t)p * LDR;
-          Real* bq = Bl + (size_t)q * LDR;
-          if (q < b && sc != (Real)0 && fabs(sc) > (Real)tol * sqrtr(sa) * sqrtr(sb)) {
+          for (int o = tpp >> 1; o > 0; o >>= 1) {
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            sc += __shfl_xor_sync(0xffffffffu, sc, o);
+          }
+          if (act && q < b && sc != (Real)0 && sc * sc > tol_r * tol_r * sa * sb) {
             Real c, s;
             jac_rotation(sa, sb, sc, &c, &s);
             if (sub == 0) s_rotated = 1;
+            Real* bp = Bl + (size_t)p * LDR;
+            Real* bq = Bl + (size_t)q * LDR;
             Real* vp = Vl + (size_t)p * LDR;
             Real* vq = Vl + (size_t)q * LDR;
 #pragma unroll 4
@@ -249,29 +261,33 @@ __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a
       continue;
     }
     for (int round = 0; round < P - 1; ++round) {
-      int p = 0, q = 0;
-      if (active) rr_pair(round, g, P, &p, &q);
-      // partial inner products over own rows
-      Real sa = 0, sb = 0, sc = 0;
-      if (active) {
-        const Real* bp = Bl + (size_t)p * LDR;
-        const Real* bq = Bl + (size_t)q * LDR;
-        for (int i = sub; i < nr; i += tpp) {
-          const Real x = bp[i], y = bq[i];
-          sa = fmar(x, x, sa);
-          sb = fmar(y, y, sb);
-          sc = fmar(x, y, sc);
+      // partial inner products over own rows, every pair
+      for (int it = 0; it < pair_iters; ++it) {
+        const int g = group + it * ngroups;
+        const bool act = g < npairs;
+        Real sa = 0, sb = 0, sc = 0;
+        if (act) {
+          int p, q;
+          rr_pair(round, g, P, &p, &q);
+          const Real* bp = Bl + (size_t)p * LDR;
+          const Real* bq = Bl + (size_t)q * LDR;
+          for (int i = sub; i < nr; i += tpp) {
+            const Real x = bp[i], y = bq[i];
+            sa = fmar(x, x, sa);
+            sb = fmar(y, y, sb);
+            sc = fmar(x, y, sc);
+          }
         }
-      }
-      for (int o = tpp >> 1; o > 0; o >>= 1) {
-        sa += __shfl_xor_sync(0xffffffffu, sa, o);
-        sb += __shfl_xor_sync(0xffffffffu, sb, o);
-        sc += __shfl_xor_sync(0xffffffffu, sc, o);
-      }
-      if (active && sub == 0) {
-        part[(size_t)g * 3] = sa;
-        part[(size_t)g * 3 + 1] = sb;
-        part[(size_t)g * 3 + 2] = sc;
+        for (int o = tpp >> 1; o > 0; o >>= 1) {
+          sa += __shfl_xor_sync(0xffffffffu, sa, o);
+          sb += __shfl_xor_sync(0xffffffffu, sb, o);
+          sc += __shfl_xor_sync(0xffffffffu, sc, o);
+        }
+        if (act && sub == 0) {
+          part[(size_t)g * 3] = sa;
+          part[(size_t)g * 3 + 1] = sb;
+          part[(size_t)g * 3 + 2] = sc;
+        }
       }
       cluster_barrier(cl, ncl);
       // owned pairs: sum the partials of all CTAs (fixed shuffle tree, so every
@@ -294,7 +310,7 @@ __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a
         if (own_lane) {
           int pp, qq;
           rr_pair(round, own_pair, P, &pp, &qq);
-          if (qq < b && ga != 0.0 && fabs(ga) > tol * sqrt(al) * sqrt(be))
+          if (qq < b && ga != 0.0 && ga * ga > tol * tol * al * be)
             jac_rotation((Real)al, (Real)be, (Real)ga, &c, &s);
         }
         if (own_lane && own_src < ncl) {
@@ -305,22 +321,24 @@ __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a
         }
       }
       cluster_barrier(cl, ncl);
-      if (active) {
+      for (int it = 0; it < pair_iters; ++it) {
+        const int g = group + it * ngroups;
+        if (g >= npairs) break;  // no shuffles below: groups may leave early
         const Real c = rot[(size_t)g * 2], s = rot[(size_t)g * 2 + 1];
         if (s != (Real)0) {
+          int p, q;
+          rr_pair(round, g, P, &p, &q);
           Real* bp = Bl + (size_t)p * LDR;
           Real* bq = Bl + (size_t)q * LDR;
+          Real* vp = Vl + (size_t)p * LDR;
+          Real* vq = Vl + (size_t)q * LDR;
           for (int i = sub; i < nr; i += tpp) {
             const Real x = bp[i], y = bq[i];
             bp[i] = fmar(c, x, -s * y);
             bq[i] = fmar(s, x, c * y);
-          }
-          Real* vp = Vl + (size_t)p * LDR;
-          Real* vq = Vl + (size_t)q * LDR;
-          for (int i = sub; i < nr; i += tpp) {
-            const Real x = vp[i], y = vq[i];
-            vp[i] = fmar(c, x, -s * y);
-            vq[i] = fmar(s, x, c * y);
+            const Real u = vp[i], w = vq[i];
+            vp[i] = fmar(c, u, -s * w);
+            vq[i] = fmar(s, u, c * w);
           }
         }
       }

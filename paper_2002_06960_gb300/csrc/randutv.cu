@@ -636,7 +636,7 @@ int randutv_householder_qr(int64_t r, int64_t c, double* panel, int64_t ld, doub
 int randutv_wy_factor(int64_t r, int64_t c, const double* W, const double* tau, double* S,
                       void* stream) {
   if (r < 1) return -1;
-  if (c < 1 || c > r) return -2;
+  if (c < 1 || c > r || c > 256) return -2;
   if (!W) return -3;
   if (!tau) return -4;
   if (!S) return -5;
