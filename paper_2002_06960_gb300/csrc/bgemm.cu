@@ -441,7 +441,7 @@ int make_tmap_bf16(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, in
 }
 
 int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int K, int pairs_mode,
-                 const BgemmOut& out, unsigned* err, cudaStream_t st) {
+                 const BgemmOut& out, unsigned* err, cudaStream_t st, int max_ctas) {
   if (M <= 0 || N <= 0) return 0;
   if (K <= 0) return RANDUTV_EUNSUPPORTED;  // no product to accumulate
   BgemmParams p;
@@ -501,7 +501,9 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
     configured = smem;
   }
   // persistent: at most one CTA per SM (the shared memory allows no more)
-  const int grid = p.ntiles < dev_info().sms ? p.ntiles : dev_info().sms;
+  int cap = dev_info().sms;
+  if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
+  const int grid = p.ntiles < cap ? p.ntiles : cap;
   ProfScope prof(K_BGEMM, 2.0 * M * (double)N * K * p.npairs,
                  2.0 * ((double)M * K * p.na + (double)K * N * p.nb) +
                      (out.mode == 0 ? 4.0 : 12.0) * M * (double)N,

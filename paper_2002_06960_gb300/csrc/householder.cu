@@ -181,9 +181,11 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
   }
 }
 
-// Number of CTAs of the panel kernel: at least 64 rows each, at most one per SM.
-int qr_blocks(int64_t r) {
-  const int sms = dev_info().sms;
+// Number of CTAs of the panel kernel: at least 64 rows each, at most one per SM
+// not reserved.
+int qr_blocks(int64_t r, int reserve_sms = 0) {
+  int sms = dev_info().sms - reserve_sms;
+  if (sms < 1) sms = 1;
   int nb = (int)((r + 63) / 64);
   if (nb > sms) nb = sms;
   if (nb < 1) nb = 1;
@@ -277,9 +279,10 @@ size_t householder_scratch_bytes(int64_t c) {
 }
 
 int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* W, double* tau,
-                          char* scratch, unsigned* bar, unsigned* err, cudaStream_t st) {
+                          char* scratch, unsigned* bar, unsigned* err, cudaStream_t st,
+                          int reserve_sms) {
   if (c <= 0) return 0;
-  const int nb = qr_blocks(r);
+  const int nb = qr_blocks(r, reserve_sms);
   QrArgs a;
   a.r = r; a.c = c; a.A = A; a.lda = lda; a.W = W; a.tau = tau;
   qr_carve(a, (double*)scratch, dev_info().sms);

@@ -17,8 +17,12 @@ int launch_dgemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
                  double* scratch, size_t scratch_bytes, cudaStream_t st);
 
 size_t householder_scratch_bytes(int64_t c);
+// SMs that the small SVD may hold while it runs beside a block step.
+constexpr int kSvdSms = 16;
+// reserve_sms: SMs to leave free (the grid then uses at most SMs - reserve_sms CTAs).
 int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* W, double* tau,
-                          char* scratch, unsigned* bar, unsigned* err, cudaStream_t st);
+                          char* scratch, unsigned* bar, unsigned* err, cudaStream_t st,
+                          int reserve_sms = 0);
 int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st);
 
 // Scratch of launch_small_svd (beside the dgemm scratch it also takes).
@@ -26,5 +30,16 @@ size_t small_svd_scratch_bytes(int b);
 int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us, double* Vs,
                      unsigned* info, void* scratch, double* gemm_scratch, size_t gemm_bytes,
                      cudaStream_t st);
+
+
+// Second stream of a device on which the small SVD of a block and its
+// fold-back run beside the next block step (non-blocking, highest priority),
+// with the two events that order it against the caller's stream.
+struct SideStream {
+  cudaStream_t st = nullptr;
+  cudaEvent_t panel = nullptr;  // main -> side: the block and its factors are final
+  cudaEvent_t svd = nullptr;    // side -> main: SVD and folds done
+};
+int side_stream(SideStream** out);
 
 }  // namespace rutv

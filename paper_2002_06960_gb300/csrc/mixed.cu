@@ -110,6 +110,8 @@ struct MixedWork {
   char* svd;
   double* dgemm;
   size_t dgemm_bytes;
+  float* tmp2;     // side stream: fold-back products
+  double* dgemm2;  // side stream: dgemm scratch
 };
 
 size_t planes_bytes(int64_t rows, int64_t cols) {
@@ -149,6 +151,8 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add(householder_scratch_bytes(b));
   add(small_svd_scratch_bytes(b));
   add(dgemm_scratch_bytes(b, b));
+  add((size_t)big * b * 4);          // tmp2
+  add(dgemm_scratch_bytes(b, b));    // dgemm2
   return s + 8192;
 }
 
@@ -185,6 +189,8 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.svd = (char*)ar.take(small_svd_scratch_bytes(b));
   w.dgemm_bytes = dgemm_scratch_bytes(b, b);
   w.dgemm = (double*)ar.take(w.dgemm_bytes);
+  w.tmp2 = (float*)ar.take((size_t)big * b * 4);
+  w.dgemm2 = (double*)ar.take(w.dgemm_bytes);
   return w;
 }
 
@@ -196,6 +202,15 @@ struct MCtx {
   MixedWork w;
   unsigned* status;
   cudaStream_t st;
+  // The small SVD and its fold-back run on the side stream beside the next
+  // block step (see the FP64 driver for the ordering argument); the row fold
+  // T(blk, k+b:) <- Us^T T(blk, k+b:) is applied on the main stream before
+  // the next right update.  While an SVD may be running, the main stream's
+  // persistent kernels leave it kSvdSms SMs.
+  SideStream* side = nullptr;
+  bool fold_pending = false;
+  int64_t fold_k = 0, fold_bi = 0;
+  int cap() const { return fold_pending ? dev_info().sms - kSvdSms : 0; }
 };
 
 // From the FP64 reflectors W64 (r x bi) and tau: W planes, S (FP64), and
@@ -219,7 +234,7 @@ int mixed_wy(MCtx& c, int64_t r, int64_t bi) {
   // WS = W S^T (r x bi): A = W (MN-major), B = S^T held as planes of S^T
   RUTV_TRY(split_f64(w.S64, bi, bi, bi, 1, w.Sp, 0, 0, c.st));
   RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 1, r, bi), opnd(w.Sp, 3, 0, 0, 0, bi, bi), (int)r, (int)bi, (int)bi, 3,
-                        out_f32(w.tmp, r), c.status, c.st));
+                        out_f32(w.tmp, r), c.status, c.st, c.cap()));
   RUTV_TRY(split_f32(w.tmp, r, bi, r, 1, w.WSt, 0, 0, c.st));
   return 0;
 }
@@ -239,6 +254,21 @@ int mixed_apply_transposed(MCtx& c, const Planes& Xt, int64_t k, int64_t r, int6
   return 0;
 }
 
+// Waits for the side stream's SVD and applies the pending row fold
+// T(blk, k+b:) <- Us^T T(blk, k+b:) on the main stream.
+int mixed_flush_fold(MCtx& c) {
+  if (!c.fold_pending) return 0;
+  c.fold_pending = false;
+  RUTV_CK(cudaStreamWaitEvent(c.st, c.side->svd, 0));
+  MixedWork& w = c.w;
+  const int64_t k = c.fold_k, bi = c.fold_bi, nc = c.n - k - bi;
+  if (nc <= 0) return 0;
+  RUTV_TRY(launch_bgemm(opnd(w.Us, 3, 0, 0, 0, bi, bi), opnd(w.T, 3, k, k + bi, 0), (int)bi, (int)nc,
+                        (int)bi, 3, out_f32(w.tmp, bi), c.status, c.st));
+  RUTV_TRY(split_f32(w.tmp, bi, bi, nc, 0, w.T, k, k + bi, c.st));
+  return 0;
+}
+
 int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
   const int64_t m = c.m, n = c.n, rm = m - k, rn = n - k;
   MixedWork& w = c.w;
@@ -247,19 +277,20 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
     RUTV_TRY(philox_normal_bf16(c.seed, (uint32_t)step, 0u, 0u, rm, bi, w.G, pad8(rm), c.st));
     // Y = T22^T G   (plane 0 of T is the BF16 copy of T22)
     RUTV_TRY(launch_bgemm(opnd(w.T, 1, k, k, 0), opnd_bf16(w.G, rm, bi, pad8(rm), 0), (int)rn,
-                          (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st));
+                          (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st, c.cap()));
     for (int it = 0; it < c.q; ++it) {
       RUTV_TRY(scaled_bf16(w.Y, rn, rn, bi, w.Yb, pad8(rn), w.scal, c.st));
       RUTV_TRY(launch_bgemm(opnd(w.T, 1, k, k, 1), opnd_bf16(w.Yb, rn, bi, pad8(rn), 0), (int)rm,
-                            (int)bi, (int)rn, 1, out_f32(w.Z, rm), c.status, c.st));
+                            (int)bi, (int)rn, 1, out_f32(w.Z, rm), c.status, c.st, c.cap()));
       RUTV_TRY(scaled_bf16(w.Z, rm, rm, bi, w.Yb, pad8(rm), w.scal, c.st));
       RUTV_TRY(launch_bgemm(opnd(w.T, 1, k, k, 0), opnd_bf16(w.Yb, rm, bi, pad8(rm), 0), (int)rn,
-                            (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st));
+                            (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st, c.cap()));
     }
     RUTV_TRY(f32_to_f64(w.Y, rn, rn, bi, w.Y64, rn, c.st));
     RUTV_TRY(launch_householder_qr(rn, bi, w.Y64, rn, w.W64, w.tau, w.qr, c.status + 2, c.status,
-                                   c.st));
+                                   c.st, c.fold_pending ? kSvdSms : 0));
     RUTV_TRY(mixed_wy(c, rn, bi));
+    RUTV_TRY(mixed_flush_fold(c));
     // X = T(:, k:) W (m x bi), then T(:, k:) -= X WS^T with X^T as planes
     RUTV_TRY(launch_bgemm(opnd(w.T, 3, 0, k, 1), opnd(w.W, 3, 0, 0, 0, rn, bi), (int)m, (int)bi, (int)rn, 3,
                           out_f32(w.X, m), c.status, c.st));
@@ -285,34 +316,36 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
     }
     if (c.want_u) RUTV_TRY(mixed_apply_transposed(c, w.Ut, k, rm, bi));
   }
-  // ---------------- small SVD (FP64) and fold-back (six-product BF16)
-  RUTV_TRY(merge_f64(w.T, k, k, bi, bi, 0, w.blk64, bi, c.st));
+  // ---------------- small SVD (FP64) and fold-back (six-product BF16), side stream
+  RUTV_TRY(mixed_flush_fold(c));  // the previous block's row fold precedes this SVD's folds
+  cudaStream_t ss = c.side->st;
+  RUTV_CK(cudaEventRecord(c.side->panel, c.st));
+  RUTV_CK(cudaStreamWaitEvent(ss, c.side->panel, 0));
+  RUTV_TRY(merge_f64(w.T, k, k, bi, bi, 0, w.blk64, bi, ss));
   RUTV_TRY(launch_small_svd((int)bi, w.blk64, bi, w.D, w.Us64, w.Vs64, c.status + 8, w.svd,
-                            w.dgemm, w.dgemm_bytes, c.st));
-  RUTV_TRY(split_f64(w.Us64, bi, bi, bi, 0, w.Us, 0, 0, c.st));
-  RUTV_TRY(split_f64(w.Vs64, bi, bi, bi, 0, w.Vs, 0, 0, c.st));
+                            w.dgemm2, w.dgemm_bytes, ss));
+  RUTV_TRY(split_f64(w.Us64, bi, bi, bi, 0, w.Us, 0, 0, ss));
+  RUTV_TRY(split_f64(w.Vs64, bi, bi, bi, 0, w.Vs, 0, 0, ss));
   if (k > 0) {  // T(0:k, blk) <- T(0:k, blk) Vs
     RUTV_TRY(launch_bgemm(opnd(w.T, 3, 0, k, 1), opnd(w.Vs, 3, 0, 0, 0, bi, bi), (int)k, (int)bi, (int)bi, 3,
-                          out_f32(w.tmp, k), c.status, c.st));
-    RUTV_TRY(split_f32(w.tmp, k, k, bi, 0, w.T, 0, k, c.st));
-  }
-  if (rn > bi) {  // T(blk, k+bi:) <- Us^T T(blk, k+bi:)
-    const int64_t nc = rn - bi;
-    RUTV_TRY(launch_bgemm(opnd(w.Us, 3, 0, 0, 0, bi, bi), opnd(w.T, 3, k, k + bi, 0), (int)bi, (int)nc,
-                          (int)bi, 3, out_f32(w.tmp, bi), c.status, c.st));
-    RUTV_TRY(split_f32(w.tmp, bi, bi, nc, 0, w.T, k, k + bi, c.st));
+                          out_f32(w.tmp2, k), c.status, ss, kSvdSms));
+    RUTV_TRY(split_f32(w.tmp2, k, k, bi, 0, w.T, 0, k, ss));
   }
   if (c.want_v) {  // V(:, blk) <- V(:, blk) Vs, i.e. V^T(blk, :) <- Vs^T V^T(blk, :)
     RUTV_TRY(launch_bgemm(opnd(w.Vs, 3, 0, 0, 0, bi, bi), opnd(w.Vt, 3, k, 0, 0), (int)bi, (int)n, (int)bi,
-                          3, out_f32(w.tmp, bi), c.status, c.st));
-    RUTV_TRY(split_f32(w.tmp, bi, bi, n, 0, w.Vt, k, 0, c.st));
+                          3, out_f32(w.tmp2, bi), c.status, ss, kSvdSms));
+    RUTV_TRY(split_f32(w.tmp2, bi, bi, n, 0, w.Vt, k, 0, ss));
   }
   if (c.want_u) {
     RUTV_TRY(launch_bgemm(opnd(w.Us, 3, 0, 0, 0, bi, bi), opnd(w.Ut, 3, k, 0, 0), (int)bi, (int)m, (int)bi,
-                          3, out_f32(w.tmp, bi), c.status, c.st));
-    RUTV_TRY(split_f32(w.tmp, bi, bi, m, 0, w.Ut, k, 0, c.st));
+                          3, out_f32(w.tmp2, bi), c.status, ss, kSvdSms));
+    RUTV_TRY(split_f32(w.tmp2, bi, bi, m, 0, w.Ut, k, 0, ss));
   }
-  RUTV_TRY(set_diag_planes(w.T, k, bi, w.D, c.st));
+  RUTV_TRY(set_diag_planes(w.T, k, bi, w.D, ss));
+  RUTV_CK(cudaEventRecord(c.side->svd, ss));
+  c.fold_pending = true;  // T(blk, k+bi:) <- Us^T T(blk, k+bi:) (empty when rn == bi)
+  c.fold_k = k;
+  c.fold_bi = bi;
   return 0;
 }
 
@@ -359,12 +392,14 @@ int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int 
   RUTV_TRY(split_f32(A, lda, m, n, 0, c.w.T, 0, 0, st));
   if (c.want_u) RUTV_TRY(set_identity_planes(c.w.Ut, st));
   if (c.want_v) RUTV_TRY(set_identity_planes(c.w.Vt, st));
+  RUTV_TRY(side_stream(&c.side));
   int step = 0;
   for (int64_t k = 0; k < p; k += b, ++step) {
     const int64_t bi = (b < p - k) ? b : p - k;
     if (max_steps >= 0 && step >= max_steps) break;
     RUTV_TRY(mixed_step(c, step, k, bi));
   }
+  RUTV_TRY(mixed_flush_fold(c));  // also joins the side stream into the caller's stream
   RUTV_TRY(merge_f32(c.w.T, 0, 0, m, n, 0, T, m, st));
   if (c.want_u) RUTV_TRY(merge_f32(c.w.Ut, 0, 0, m, m, 1, U, m, st));
   if (c.want_v) RUTV_TRY(merge_f32(c.w.Vt, 0, 0, n, n, 1, V, n, st));

@@ -45,8 +45,10 @@ struct BgemmOut {
 
 // pairs_mode 1: one BF16 product of plane 0 of A and B.  pairs_mode 3: the
 // six products A_i B_j with i + j <= 2 of three planes each (FP32 accuracy).
+// max_ctas: upper bound on the persistent grid (0 = one CTA per SM).
 int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int K,
-                 int pairs_mode, const BgemmOut& out, unsigned* err, cudaStream_t st);
+                 int pairs_mode, const BgemmOut& out, unsigned* err, cudaStream_t st,
+                 int max_ctas = 0);
 
 int make_tmap_bf16(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols,
                    int64_t ld, int box_cols);

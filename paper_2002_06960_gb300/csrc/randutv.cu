@@ -274,6 +274,8 @@ Plan make_plan(int64_t m, int64_t n, int64_t b) {
   add(householder_scratch_bytes(b));
   add(small_svd_scratch_bytes(b));
   add(dgemm_scratch_bytes(p.big, b));
+  add(big);                             // tmp of the SVD stream
+  add(dgemm_scratch_bytes(p.big, b));   // dgemm scratch of the SVD stream
   p.bytes = bytes + 4096;
   return p;
 }
@@ -284,6 +286,8 @@ struct Work {
   char* svd;
   double* gemm;
   size_t gemm_bytes;
+  double* tmp2;   // SVD stream: fold-back products
+  double* gemm2;  // SVD stream: dgemm scratch
 };
 
 Work carve(Arena& ar, const Plan& p) {
@@ -307,8 +311,12 @@ Work carve(Arena& ar, const Plan& p) {
   w.svd = (char*)ar.take(small_svd_scratch_bytes(p.b));
   w.gemm_bytes = dgemm_scratch_bytes(p.big, p.b);
   w.gemm = (double*)ar.take(w.gemm_bytes);
+  w.tmp2 = (double*)ar.take(big);
+  w.gemm2 = (double*)ar.take(w.gemm_bytes);
   return w;
 }
+
+
 
 // ---------------------------------------------------------------- the step
 
@@ -321,6 +329,9 @@ struct Ctx {
   Work w;
   unsigned* status;  // [0] err, [1] site, [2..3] barrier
   cudaStream_t st;
+  SideStream* side;
+  bool fold_pending = false;  // row fold of an earlier block still to apply
+  int64_t fold_k = 0, fold_bi = 0;
 };
 
 int gemm(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
@@ -338,6 +349,26 @@ int wy_and_ws(Ctx& c, int64_t r, int64_t bi) {
   return 0;
 }
 
+// Waits for the side stream's SVD and applies the pending row fold
+// T(blk, k+b:) <- Us^T T(blk, k+b:) of that block on the main stream.
+int flush_fold(Ctx& c) {
+  if (!c.fold_pending) return 0;
+  c.fold_pending = false;
+  RUTV_CK(cudaStreamWaitEvent(c.st, c.side->svd, 0));
+  const int64_t k = c.fold_k, bi = c.fold_bi, nc = c.n - k - bi;
+  if (nc <= 0) return 0;
+  double* Tr = c.T + k + (k + bi) * c.ldt;  // T(blk, k+bi:)
+  RUTV_TRY(gemm(c, true, false, bi, nc, bi, 1.0, c.w.Us, bi, Tr, c.ldt, 0.0, c.w.tmp, bi));
+  RUTV_TRY(copy2d(Tr, c.ldt, c.w.tmp, bi, bi, nc, c.st));
+  return 0;
+}
+
+int side_gemm(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, const double* A,
+              int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc) {
+  return launch_dgemm(ta, tb, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, c.w.gemm2,
+                      c.w.gemm_bytes, c.side->st);
+}
+
 int block_step(Ctx& c, int step, int64_t k, int64_t bi) {
   const int64_t m = c.m, n = c.n, ldt = c.ldt;
   const int64_t rm = m - k, rn = n - k;
@@ -352,9 +383,11 @@ int block_step(Ctx& c, int step, int64_t k, int64_t bi) {
       RUTV_TRY(gemm(c, false, false, rm, bi, rn, 1.0, T22, ldt, w.Y, rn, 0.0, w.Z, rm));
       RUTV_TRY(gemm(c, true, false, rn, bi, rm, 1.0, T22, ldt, w.Z, rm, 0.0, w.Y, rn));
     }
+    // the previous block's SVD may still hold SMs: leave them to it
     RUTV_TRY(launch_householder_qr(rn, bi, w.Y, rn, w.W, w.tau, w.qr, c.status + 2, c.status,
-                                   c.st));
+                                   c.st, c.fold_pending ? kSvdSms : 0));
     RUTV_TRY(wy_and_ws(c, rn, bi));
+    RUTV_TRY(flush_fold(c));
     double* Tk = T + k * ldt;
     RUTV_TRY(gemm(c, false, false, m, bi, rn, 1.0, Tk, ldt, w.W, rn, 0.0, w.X, m));
     RUTV_TRY(gemm(c, false, true, m, rn, bi, -1.0, w.X, m, w.WS, rn, 1.0, Tk, ldt));
@@ -381,37 +414,73 @@ int block_step(Ctx& c, int step, int64_t k, int64_t bi) {
       RUTV_TRY(gemm(c, false, true, m, rm, bi, -1.0, w.X, m, w.WS, rm, 1.0, Uk, m));
     }
   }
-  // ---- small SVD of the diagonal block and its fold-back
-  RUTV_TRY(launch_small_svd((int)bi, T22, ldt, w.D, w.Us, w.Vs, c.status + 8, w.svd, w.gemm,
-                            w.gemm_bytes, c.st));
+  // ---- small SVD of the diagonal block and its fold-back, on the side stream
+  RUTV_TRY(flush_fold(c));  // the previous block's row fold precedes this SVD's folds
+  cudaStream_t ss = c.side->st;
+  RUTV_CK(cudaEventRecord(c.side->panel, c.st));
+  RUTV_CK(cudaStreamWaitEvent(ss, c.side->panel, 0));
+  RUTV_TRY(launch_small_svd((int)bi, T22, ldt, w.D, w.Us, w.Vs, c.status + 8, w.svd, w.gemm2,
+                            w.gemm_bytes, ss));
   if (k > 0) {
     double* Tc = T + k * ldt;  // T(0:k, blk)
-    RUTV_TRY(gemm(c, false, false, k, bi, bi, 1.0, Tc, ldt, w.Vs, bi, 0.0, w.tmp, k));
-    RUTV_TRY(copy2d(Tc, ldt, w.tmp, k, k, bi, c.st));
-  }
-  if (rn > bi) {
-    double* Tr = T + k + (k + bi) * ldt;  // T(blk, k+bi:)
-    const int64_t nc = rn - bi;
-    RUTV_TRY(gemm(c, true, false, bi, nc, bi, 1.0, w.Us, bi, Tr, ldt, 0.0, w.tmp, bi));
-    RUTV_TRY(copy2d(Tr, ldt, w.tmp, bi, bi, nc, c.st));
+    RUTV_TRY(side_gemm(c, false, false, k, bi, bi, Tc, ldt, w.Vs, bi, w.tmp2, k));
+    RUTV_TRY(copy2d(Tc, ldt, w.tmp2, k, k, bi, ss));
   }
   if (c.V) {
     double* Vb = c.V + k * n;
-    RUTV_TRY(gemm(c, false, false, n, bi, bi, 1.0, Vb, n, w.Vs, bi, 0.0, w.tmp, n));
-    RUTV_TRY(copy2d(Vb, n, w.tmp, n, n, bi, c.st));
+    RUTV_TRY(side_gemm(c, false, false, n, bi, bi, Vb, n, w.Vs, bi, w.tmp2, n));
+    RUTV_TRY(copy2d(Vb, n, w.tmp2, n, n, bi, ss));
   }
   if (c.U) {
     double* Ub = c.U + k * m;
-    RUTV_TRY(gemm(c, false, false, m, bi, bi, 1.0, Ub, m, w.Us, bi, 0.0, w.tmp, m));
-    RUTV_TRY(copy2d(Ub, m, w.tmp, m, m, bi, c.st));
+    RUTV_TRY(side_gemm(c, false, false, m, bi, bi, Ub, m, w.Us, bi, w.tmp2, m));
+    RUTV_TRY(copy2d(Ub, m, w.tmp2, m, m, bi, ss));
   }
-  set_diag_block_kernel<<<grid_for(bi * bi), 256, 0, c.st>>>(bi, w.D, T22, ldt);
+  set_diag_block_kernel<<<grid_for(bi * bi), 256, 0, ss>>>(bi, w.D, T22, ldt);
   note_launch();
   RUTV_CK(cudaGetLastError());
+  RUTV_CK(cudaEventRecord(c.side->svd, ss));
+  c.fold_pending = true;  // T(blk, k+bi:) <- Us^T T(blk, k+bi:) (empty when rn == bi)
+  c.fold_k = k;
+  c.fold_bi = bi;
   return 0;
 }
 
 }  // namespace
+}  // namespace rutv
+
+namespace rutv {
+
+// The small SVD of a block and its fold-back run on a second stream, beside
+// the next block step: nothing of step k+1 before its right update reads
+// what they write.  One fold, T(blk, k+b:) <- Us^T T(blk, k+b:), writes
+// entries that step k+1's right update also writes; the main stream applies
+// it itself, after waiting for the SVD, just before that update (or before
+// the next SVD starts, or at the end of the call).  Every entry thus sees the
+// same operations in the same order as in a serial run, and the results are
+// bitwise the same.  The side stream is non-blocking (no implicit ordering
+// with the legacy default stream) and of the highest priority; one per
+// device, with its two events.
+std::mutex g_side_mu;
+SideStream g_side[64];
+
+int side_stream(SideStream** out) {
+  int dev = 0;
+  RUTV_CK(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) return RANDUTV_EUNSUPPORTED;
+  std::lock_guard<std::mutex> lk(g_side_mu);
+  SideStream& s = g_side[dev];
+  if (!s.st) {
+    int least = 0, greatest = 0;
+    RUTV_CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    RUTV_CK(cudaStreamCreateWithPriority(&s.st, cudaStreamNonBlocking, greatest));
+    RUTV_CK(cudaEventCreateWithFlags(&s.panel, cudaEventDisableTiming));
+    RUTV_CK(cudaEventCreateWithFlags(&s.svd, cudaEventDisableTiming));
+  }
+  *out = &s;
+  return 0;
+}
+
 }  // namespace rutv
 
 // ================================================================= C-ABI
@@ -555,6 +624,7 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
     if (U) RUTV_TRY(set_identity(m, m, U, m, st));
     if (V) RUTV_TRY(set_identity(n, n, V, n, st));
   }
+  RUTV_TRY(side_stream(&c.side));
   int step = 0;
   for (int64_t k = 0; k < p; k += bb, ++step) {
     const int64_t bi = (bb < p - k) ? bb : p - k;
@@ -562,6 +632,7 @@ int randutv_factor_ex(int64_t m, int64_t n, const double* A, int64_t lda, int b,
     if (max_steps >= 0 && step >= max_steps) break;
     RUTV_TRY(block_step(c, step, k, bi));
   }
+  RUTV_TRY(flush_fold(c));  // also joins the side stream into the caller's stream
   return 0;
 }
 
