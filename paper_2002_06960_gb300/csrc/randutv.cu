@@ -275,7 +275,7 @@ Plan make_plan(int64_t m, int64_t n, int64_t b) {
   add(small_svd_scratch_bytes(b));
   add(dgemm_scratch_bytes(p.big, b));
   add(big);                             // tmp of the SVD stream
-  add(dgemm_scratch_bytes(p.big, b));   // dgemm scratch of the SVD stream
+  add(dgemm_scratch_bytes(b, b));       // dgemm scratch of the SVD stream (K = b products)
   p.bytes = bytes + 4096;
   return p;
 }
@@ -288,6 +288,7 @@ struct Work {
   size_t gemm_bytes;
   double* tmp2;   // SVD stream: fold-back products
   double* gemm2;  // SVD stream: dgemm scratch
+  size_t gemm2_bytes;
 };
 
 Work carve(Arena& ar, const Plan& p) {
@@ -312,7 +313,8 @@ Work carve(Arena& ar, const Plan& p) {
   w.gemm_bytes = dgemm_scratch_bytes(p.big, p.b);
   w.gemm = (double*)ar.take(w.gemm_bytes);
   w.tmp2 = (double*)ar.take(big);
-  w.gemm2 = (double*)ar.take(w.gemm_bytes);
+  w.gemm2_bytes = dgemm_scratch_bytes(p.b, p.b);
+  w.gemm2 = (double*)ar.take(w.gemm2_bytes);
   return w;
 }
 
@@ -366,7 +368,7 @@ int flush_fold(Ctx& c) {
 int side_gemm(Ctx& c, bool ta, bool tb, int64_t M, int64_t N, int64_t K, const double* A,
               int64_t lda, const double* B, int64_t ldb, double* C, int64_t ldc) {
   return launch_dgemm(ta, tb, M, N, K, 1.0, A, lda, B, ldb, 0.0, C, ldc, c.w.gemm2,
-                      c.w.gemm_bytes, c.side->st);
+                      c.w.gemm2_bytes, c.side->st);
 }
 
 int block_step(Ctx& c, int step, int64_t k, int64_t bi) {
@@ -420,7 +422,7 @@ int block_step(Ctx& c, int step, int64_t k, int64_t bi) {
   RUTV_CK(cudaEventRecord(c.side->panel, c.st));
   RUTV_CK(cudaStreamWaitEvent(ss, c.side->panel, 0));
   RUTV_TRY(launch_small_svd((int)bi, T22, ldt, w.D, w.Us, w.Vs, c.status + 8, w.svd, w.gemm2,
-                            w.gemm_bytes, ss));
+                            w.gemm2_bytes, ss));
   if (k > 0) {
     double* Tc = T + k * ldt;  // T(0:k, blk)
     RUTV_TRY(side_gemm(c, false, false, k, bi, bi, Tc, ldt, w.Vs, bi, w.tmp2, k));
