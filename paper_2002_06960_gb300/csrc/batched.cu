@@ -24,7 +24,8 @@ namespace {
 
 constexpr int BT = 256;          // threads per CTA
 constexpr int BMAX = 64;         // largest block size of the batched path
-constexpr int GT = 64, GK = 16;  // CTA GEMM tile (GT x GT outputs, GK deep)
+constexpr int GT = 64, GK = 32;  // CTA GEMM tile (GT x GT outputs, GK deep per stage)
+constexpr int GLD = GT + 1;      // row stride of the tiles in shared memory (conflict-free)
 constexpr int NWARP = BT / 32;
 
 struct BatchDesc {
@@ -50,11 +51,18 @@ struct BatchArgs {
 };
 
 struct Smem {
-  float gA[GK][GT + 1];
-  float gB[GK][GT + 1];
-  float svB[BMAX][BMAX + 1];  // column j at svB[j][i]
-  float svV[BMAX][BMAX + 1];
-  double S[BMAX][BMAX + 1];   // S(i, j) at S[j][i], FP64
+  // The GEMM tiles and the WY / SVD arrays are never live at the same time.
+  union {
+    struct {
+      float gA[2][GK][GLD];  // A tile, k-major: gA[buf][k][m]
+      float gB[2][GK][GLD];  // B tile, k-major: gB[buf][k][n]
+    };
+    struct {
+      float svB[BMAX][BMAX + 1];  // column j at svB[j][i]
+      float svV[BMAX][BMAX + 1];
+      double S[BMAX][BMAX + 1];   // S(i, j) at S[j][i], FP64
+    };
+  };
   double tau[BMAX];
   float wv[BMAX];
   float D[BMAX];
@@ -67,11 +75,15 @@ struct Smem {
 
 // ------------------------------------------------------------ CTA GEMM
 // C = alpha op(A) op(B) + beta C (FP32, column-major); C must not alias A, B.
+// 64 x 64 output tiles, 4 x 4 per thread (rows tx + 16 i, columns ty + 16 j),
+// K in stages of 32 through two shared-memory buffers: the global loads of
+// stage s + 1 are in flight (held in registers) while stage s is multiplied.
 template <bool TA, bool TB>
 __device__ void cta_gemm(int M, int N, int K, float alpha, const float* __restrict__ A, int64_t lda,
                          const float* __restrict__ B, int64_t ldb, float beta, float* C,
                          int64_t ldc, Smem& sm) {
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  constexpr int PER = GT * GK / BT;  // elements of each tile a thread loads per stage
   for (int m0 = 0; m0 < M; m0 += GT) {
     for (int n0 = 0; n0 < N; n0 += GT) {
       float acc[4][4];
@@ -79,44 +91,68 @@ __device__ void cta_gemm(int M, int N, int K, float alpha, const float* __restri
       for (int i = 0; i < 4; ++i)
 #pragma unroll
         for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-      for (int k0 = 0; k0 < K; k0 += GK) {
-        for (int e = tid; e < GT * GK; e += BT) {
+      float ra[PER], rb[PER];
+      // element e = tid + BT t of a tile; the fast index follows the
+      // contiguous direction of the source, so the global loads coalesce
+      auto load = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < PER; ++t) {
+          const int e = tid + BT * t;
           int mm, kk;
           if (!TA) { mm = e % GT; kk = e / GT; } else { kk = e % GK; mm = e / GK; }
           const int gm = m0 + mm, gk = k0 + kk;
-          sm.gA[kk][mm] = (gm < M && gk < K)
-                              ? (TA ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda])
-                              : 0.f;
+          ra[t] = (gm < M && gk < K) ? (TA ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda])
+                                     : 0.f;
           int nn, kb;
           if (!TB) { kb = e % GK; nn = e / GK; } else { nn = e % GT; kb = e / GT; }
           const int gn = n0 + nn, gkb = k0 + kb;
-          sm.gB[kb][nn] = (gn < N && gkb < K)
-                              ? (TB ? B[gn + (int64_t)gkb * ldb] : B[gkb + (int64_t)gn * ldb])
-                              : 0.f;
+          rb[t] = (gn < N && gkb < K) ? (TB ? B[gn + (int64_t)gkb * ldb] : B[gkb + (int64_t)gn * ldb])
+                                      : 0.f;
         }
-        __syncthreads();
+      };
+      auto store = [&](int buf) {
 #pragma unroll
+        for (int t = 0; t < PER; ++t) {
+          const int e = tid + BT * t;
+          int mm, kk;
+          if (!TA) { mm = e % GT; kk = e / GT; } else { kk = e % GK; mm = e / GK; }
+          sm.gA[buf][kk][mm] = ra[t];
+          int nn, kb;
+          if (!TB) { kb = e % GK; nn = e / GK; } else { nn = e % GT; kb = e / GT; }
+          sm.gB[buf][kb][nn] = rb[t];
+        }
+      };
+      load(0);
+      store(0);
+      __syncthreads();
+      int buf = 0;
+      for (int k0 = 0; k0 < K; k0 += GK) {
+        const bool more = k0 + GK < K;
+        if (more) load(k0 + GK);
+#pragma unroll 8
         for (int k = 0; k < GK; ++k) {
           float a[4], bb[4];
 #pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = sm.gA[k][ty + 16 * i];
+          for (int i = 0; i < 4; ++i) a[i] = sm.gA[buf][k][tx + 16 * i];
 #pragma unroll
-          for (int j = 0; j < 4; ++j) bb[j] = sm.gB[k][tx + 16 * j];
+          for (int j = 0; j < 4; ++j) bb[j] = sm.gB[buf][k][ty + 16 * j];
 #pragma unroll
           for (int i = 0; i < 4; ++i)
 #pragma unroll
             for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
         }
+        if (more) store(buf ^ 1);  // the other buffer was released by the last barrier
         __syncthreads();
+        buf ^= 1;
       }
 #pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        const int m = m0 + ty + 16 * i;
-        if (m >= M) continue;
+      for (int j = 0; j < 4; ++j) {
+        const int n = n0 + ty + 16 * j;
+        if (n >= N) continue;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int n = n0 + tx + 16 * j;
-          if (n >= N) continue;
+        for (int i = 0; i < 4; ++i) {
+          const int m = m0 + tx + 16 * i;
+          if (m >= M) continue;
           float* c = C + m + (int64_t)n * ldc;
           float v = alpha * acc[i][j];
           if (beta != 0.f) v = fmaf(beta, *c, v);
@@ -639,7 +675,7 @@ __device__ int factor_one(const BatchDesc& d, uint64_t seed, Work& w, Smem& sm) 
   return 0;
 }
 
-__global__ void __launch_bounds__(BT) batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(BT, 2) batched_kernel(BatchArgs a) {
   extern __shared__ __align__(16) unsigned char smraw[];
   Smem& sm = *reinterpret_cast<Smem*>(smraw);
   __shared__ int s_idx;

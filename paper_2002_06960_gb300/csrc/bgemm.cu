@@ -352,6 +352,9 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
       }
       // warp-uniform: the lanes must not split before the next tcgen05.ld
       if (__any_sync(0xffffffffu, !ok || *(volatile unsigned*)p.err != 0)) break;
+      // the tile's sum, rounded once to FP32 (frees the compensation registers)
+#pragma unroll
+      for (int i = 0; i < BN; ++i) sum[i] += cmp[i];
       const int row = m0 + qd * 32 + lane;
       if (row < p.M) {
         if (p.mode == 0) {
@@ -360,32 +363,50 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
             const int col = n0 + i;
             if (col < p.N) {
               float* dst = p.C + (int64_t)row + (int64_t)col * p.ldc;
-              float r = p.alpha * (sum[i] + cmp[i]);
+              float r = p.alpha * sum[i];
               if (p.beta != 0.f) r = fmaf(p.beta, *dst, r);
               *dst = r;
             }
           }
         } else {
+          // Read-modify-write of the three planes, four columns at a time:
+          // the 12 loads of a group are issued together, so the memory
+          // latency is paid once per group rather than once per column.
+          constexpr int CG = 4;
 #pragma unroll
-          for (int i = 0; i < BN; ++i) {
-            const int col = n0 + i;
-            if (col < p.N) {
-              const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
-              // X + alpha acc carried as hi + lo, then split into three planes
-              const float x0 = __bfloat162float(p.P0[o]);
-              const float xr = __bfloat162float(p.P1[o]) + __bfloat162float(p.P2[o]);
-              float hi, lo;
-              two_sum(x0, p.alpha * sum[i], hi, lo);
-              lo += xr + p.alpha * cmp[i];
-              float y, ey;
-              two_sum(hi, lo, y, ey);
-              const __nv_bfloat16 h0 = __float2bfloat16_rn(y);
-              const float r = (y - __bfloat162float(h0)) + ey;
-              const __nv_bfloat16 h1 = __float2bfloat16_rn(r);
-              const __nv_bfloat16 h2 = __float2bfloat16_rn(r - __bfloat162float(h1));
-              p.P0[o] = h0;
-              p.P1[o] = h1;
-              p.P2[o] = h2;
+          for (int c0 = 0; c0 < BN; c0 += CG) {
+            __nv_bfloat16 q0[CG], q1[CG], q2[CG];
+#pragma unroll
+            for (int i = 0; i < CG; ++i) {
+              const int col = n0 + c0 + i;
+              if (col < p.N) {
+                const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
+                q0[i] = p.P0[o];
+                q1[i] = p.P1[o];
+                q2[i] = p.P2[o];
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < CG; ++i) {
+              const int col = n0 + c0 + i;
+              if (col < p.N) {
+                const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
+                // X + alpha acc carried as hi + lo, then split into three planes
+                const float x0 = __bfloat162float(q0[i]);
+                const float xr = __bfloat162float(q1[i]) + __bfloat162float(q2[i]);
+                float hi, lo;
+                two_sum(x0, p.alpha * sum[c0 + i], hi, lo);
+                lo += xr;
+                float y, ey;
+                two_sum(hi, lo, y, ey);
+                const __nv_bfloat16 h0 = __float2bfloat16_rn(y);
+                const float r = (y - __bfloat162float(h0)) + ey;
+                const __nv_bfloat16 h1 = __float2bfloat16_rn(r);
+                const __nv_bfloat16 h2 = __float2bfloat16_rn(r - __bfloat162float(h1));
+                p.P0[o] = h0;
+                p.P1[o] = h1;
+                p.P2[o] = h2;
+              }
             }
           }
         }
