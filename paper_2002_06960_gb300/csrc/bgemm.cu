@@ -37,6 +37,10 @@ constexpr int THREADS = 192;
 constexpr int A_TILE = BM * BK * 2;  // 16 KiB
 constexpr int B_TILE = BN * BK * 2;  // 8 KiB
 constexpr int kTmemCols = 4 * BN;    // two buffers x (leading, correction) accumulators
+constexpr int C_ELEMS = BM * BN;     // one output plane tile (mode 1)
+constexpr int C_TILE = C_ELEMS * 2;  // its bytes
+constexpr int C_ROWS = 32;           // rows of one epilogue warp's slice (box C_ROWS x BN)
+constexpr int C_SLICE = C_ROWS * BN; // elements of a slice, column-major (ld C_ROWS)
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
@@ -149,6 +153,26 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// TMA store of a 2-D box from shared memory (bulk-group completion).
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+          (uint64_t)map),
+      "r"(smem_u32(src)), "r"(x), "r"(y)
+      : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+// wait until the committed bulk stores have finished reading shared memory
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+}
+// wait until the committed bulk stores are complete
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// generic-proxy writes to shared memory made visible to the async (TMA) proxy
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
@@ -163,6 +187,7 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 struct BgemmParams {
   CUtensorMap ta[3];
   CUtensorMap tb[3];
+  CUtensorMap tc[3];   // mode 1: the output planes, box C_ROWS x BN, no swizzle
   int M, N, K;
   int tiles_n, ntiles, ksteps;
   int na, nb, npairs;
@@ -197,12 +222,17 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
   // 1024-byte aligned tile area
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int per_stage = p.na * A_TILE + p.nb * B_TILE;
-  uint64_t* full = (uint64_t*)(smem + (size_t)p.stages * per_stage);
+  // mode 1: the output tile's three planes (column-major BM x BN each) follow the stages
+  __nv_bfloat16* ctile = (__nv_bfloat16*)(smem + (size_t)p.stages * per_stage);
+  const size_t ctile_bytes = (p.mode == 1) ? (size_t)C_TILE * 3 : 0;
+  uint64_t* full = (uint64_t*)(smem + (size_t)p.stages * per_stage + ctile_bytes);
   uint64_t* empty = full + p.stages;
   uint64_t* acc_full = empty + p.stages;  // [2]
   uint64_t* acc_empty = acc_full + 2;     // [2]
   uint64_t* mma_done = acc_empty + 2;
-  uint32_t* tmem_slot = (uint32_t*)(mma_done + 1);
+  uint64_t* cfull = mma_done + 1;         // mode 1: output planes loaded
+  uint64_t* cfree = cfull + 1;            // mode 1: output planes stored (buffer free)
+  uint32_t* tmem_slot = (uint32_t*)(cfree + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ksteps = p.ksteps;
@@ -217,6 +247,8 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
       mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
     }
     mbar_init(mma_done, 1);
+    mbar_init(cfull, 1);
+    mbar_init(cfree, 4);  // one arrival per epilogue warp
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -233,7 +265,9 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
   if (warp == 0) {
     // ------------------------------------------------------------ producer
     if (lane == 0) {
-      int g = 0;  // K steps issued over all tiles of this CTA
+      int g = 0;   // K steps issued over all tiles of this CTA
+      int tl = 0;  // tiles of this CTA
+      int cl = 0;  // output-plane loads issued
       bool run = true;
       for (int tile = blockIdx.x; run && tile < p.ntiles; tile += gridDim.x) {
         const int m0 = (tile / p.tiles_n) * BM, n0 = (tile % p.tiles_n) * BN;
@@ -261,11 +295,26 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
             tma_load_2d(dst, &p.tb[j], &full[s], p.b_x0 + k0, p.b_y0 + n0);
           }
         }
+        if (run && p.mode == 1) {
+          // output planes of this tile, once the previous tile's have been stored
+          if (tl > 0 && !mbar_wait(cfree, (uint32_t)((tl - 1) & 1), p.err, 17)) {
+            run = false;
+          } else {
+            mbar_expect_tx(cfull, (uint32_t)(3 * C_TILE));
+            for (int i = 0; i < 3; ++i)
+              for (int sl = 0; sl < BM / C_ROWS; ++sl)
+                tma_load_2d(ctile + (size_t)i * C_ELEMS + (size_t)sl * C_SLICE, &p.tc[i], cfull,
+                            m0 + sl * C_ROWS, n0);
+            ++cl;
+          }
+        }
+        ++tl;
       }
       // let every copy issued land before the CTA can exit
       for (int k = (g > p.stages ? g - p.stages : 0); k < g; ++k) {
         mbar_wait(&full[k % p.stages], (uint32_t)((k / p.stages) & 1), p.err, 12);
       }
+      if (cl > 0) mbar_wait(cfull, (uint32_t)((cl - 1) & 1), p.err, 18);
     }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
@@ -316,6 +365,7 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     const int qd = warp & 3;  // TMEM lane quadrant this warp may access
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
     int g = 0;
+    int tl = 0;  // tiles of this CTA
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
       const int m0 = (tile / p.tiles_n) * BM, n0 = (tile % p.tiles_n) * BN;
@@ -368,50 +418,49 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
               *dst = r;
             }
           }
-        } else {
-          // Read-modify-write of the three planes, four columns at a time:
-          // the 12 loads of a group are issued together, so the memory
-          // latency is paid once per group rather than once per column.
-          constexpr int CG = 4;
-#pragma unroll
-          for (int c0 = 0; c0 < BN; c0 += CG) {
-            __nv_bfloat16 q0[CG], q1[CG], q2[CG];
-#pragma unroll
-            for (int i = 0; i < CG; ++i) {
-              const int col = n0 + c0 + i;
-              if (col < p.N) {
-                const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
-                q0[i] = p.P0[o];
-                q1[i] = p.P1[o];
-                q2[i] = p.P2[o];
-              }
-            }
-#pragma unroll
-            for (int i = 0; i < CG; ++i) {
-              const int col = n0 + c0 + i;
-              if (col < p.N) {
-                const int64_t o = (int64_t)row + (int64_t)col * p.ldp;
-                // X + alpha acc carried as hi + lo, then split into three planes
-                const float x0 = __bfloat162float(q0[i]);
-                const float xr = __bfloat162float(q1[i]) + __bfloat162float(q2[i]);
-                float hi, lo;
-                two_sum(x0, p.alpha * sum[c0 + i], hi, lo);
-                lo += xr;
-                float y, ey;
-                two_sum(hi, lo, y, ey);
-                const __nv_bfloat16 h0 = __float2bfloat16_rn(y);
-                const float r = (y - __bfloat162float(h0)) + ey;
-                const __nv_bfloat16 h1 = __float2bfloat16_rn(r);
-                const __nv_bfloat16 h2 = __float2bfloat16_rn(r - __bfloat162float(h1));
-                p.P0[o] = h0;
-                p.P1[o] = h1;
-                p.P2[o] = h2;
-              }
-            }
-          }
         }
       }
+      if (p.mode == 1) {
+        // this warp's 32 rows of the tile's planes, in shared memory (zero
+        // past the matrix edge); each warp stores its own slice back, so the
+        // epilogue warps never wait on one another
+        const bool w = mbar_wait(cfull, (uint32_t)(tl & 1), p.err, 19);
+        if (__any_sync(0xffffffffu, !w)) break;
+        __nv_bfloat16* sl0 = ctile + (size_t)qd * C_SLICE;
+#pragma unroll
+        for (int i = 0; i < BN; ++i) {
+          const int o = i * C_ROWS + lane;
+          // X + alpha acc carried as hi + lo, then split into three planes
+          const float x0 = __bfloat162float(sl0[o]);
+          const float xr = __bfloat162float(sl0[C_ELEMS + o]) + __bfloat162float(sl0[2 * C_ELEMS + o]);
+          float hi, lo;
+          two_sum(x0, p.alpha * sum[i], hi, lo);
+          lo += xr;
+          float y, ey;
+          two_sum(hi, lo, y, ey);
+          const __nv_bfloat16 h0 = __float2bfloat16_rn(y);
+          const float rr = (y - __bfloat162float(h0)) + ey;
+          const __nv_bfloat16 h1 = __float2bfloat16_rn(rr);
+          const __nv_bfloat16 h2 = __float2bfloat16_rn(rr - __bfloat162float(h1));
+          sl0[o] = h0;
+          sl0[C_ELEMS + o] = h1;
+          sl0[2 * C_ELEMS + o] = h2;
+        }
+        fence_proxy_async();  // the writes above are read by the TMA stores below
+        __syncwarp();
+        if (lane == 0) {
+          for (int i = 0; i < 3; ++i)
+            tma_store_2d(&p.tc[i], sl0 + (size_t)i * C_ELEMS, m0 + qd * C_ROWS, n0);
+          bulk_commit();
+          bulk_wait_read();  // this slice may be overwritten from here on
+          mbar_arrive(cfree);
+        }
+        __syncwarp();
+      }
+      ++tl;
     }
+    // this warp's last stores must be complete before the CTA exits
+    if (p.mode == 1 && lane == 0) bulk_wait_all();
   }
 
   // teardown: all MMAs must have completed before TMEM is released
@@ -443,6 +492,26 @@ int get_encode() {
 
 // Tensor map of a column-major BF16 matrix (rows x cols, ld elements), box
 // {64 rows, box_cols columns}, 128-byte swizzle.  ld must be a multiple of 8.
+namespace {
+int make_tmap_box(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols,
+                  int64_t ld, int box_rows, int box_cols, CUtensorMapSwizzle swz) {
+  RUTV_TRY(get_encode());
+  if (((uintptr_t)base & 15) || (ld % 8) != 0) return RANDUTV_EUNSUPPORTED;
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)box_cols};
+  cuuint32_t estr[2] = {1u, 1u};
+  CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void*)base, dims, strides, box,
+                        estr, CU_TENSOR_MAP_INTERLEAVE_NONE, swz,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    set_last_error("cuTensorMapEncodeTiled failed");
+    return RANDUTV_ECUDA;
+  }
+  return 0;
+}
+}  // namespace
+
 int make_tmap_bf16(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols,
                    int64_t ld, int box_cols) {
   RUTV_TRY(get_encode());
@@ -496,11 +565,18 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.b_x0 = (int)B.x0;
   p.b_y0 = (int)B.y0;
   const int per_stage = p.na * A_TILE + p.nb * B_TILE;
-  int stages = (216 * 1024) / per_stage;
+  // mode 1 keeps the output tile's three planes in shared memory (TMA in and out)
+  const size_t ctile_bytes = (out.mode == 1) ? (size_t)3 * C_TILE : 0;
+  int stages = (int)((216 * 1024 - ctile_bytes) / per_stage);
   if (stages > 8) stages = 8;
   if (stages < 1) stages = 1;
   p.stages = stages;
   p.mode = out.mode;
+  if (out.mode == 1) {
+    for (int i = 0; i < 3; ++i)
+      RUTV_TRY(make_tmap_box(&p.tc[i], out.planes[i], M, N, out.ldp, C_ROWS, BN,
+                             CU_TENSOR_MAP_SWIZZLE_NONE));
+  }
   p.alpha = out.alpha;
   p.beta = out.beta;
   p.C = out.C;
@@ -514,7 +590,7 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.tiles_n = (N + BN - 1) / BN;
   p.ntiles = tiles_m * p.tiles_n;
   p.ksteps = (K + BK - 1) / BK;
-  const size_t smem = 1024 + (size_t)stages * per_stage + (2 * stages + 5) * 8 + 16;
+  const size_t smem = 1024 + (size_t)stages * per_stage + ctile_bytes + (2 * stages + 7) * 8 + 16;
   static size_t configured = 0;
   if (smem > configured) {
     RUTV_CK(cudaFuncSetAttribute(bgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
