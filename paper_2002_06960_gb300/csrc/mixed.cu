@@ -105,7 +105,9 @@ struct MixedWork {
   Planes W, WSt, Xp, Sp, Us, Vs; // small operands as planes
   __nv_bfloat16 *G, *Yb;        // BF16 sketch operands
   float *Y, *Z, *X, *tmp, *scal;
-  double *Y64, *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64, *WS64;
+  double *Y64, *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64;
+  double* W2;        // blocked panel QR: reflectors of the second half (ld r - h)
+  double *qrX, *qrY; // blocked panel QR: W1^T P2 and S1^T W1^T P2
   char* qr;
   char* svd;
   double* dgemm;
@@ -145,7 +147,8 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add((size_t)pad8(big) * b * 2); // Yb
   for (int i = 0; i < 4; ++i) add((size_t)big * b * 4);  // Y, Z, X, tmp
   add(256);                       // scal
-  for (int i = 0; i < 3; ++i) add((size_t)big * b * 8);  // Y64, W64, WS64
+  for (int i = 0; i < 3; ++i) add((size_t)big * b * 8);  // Y64, W64, W2
+  for (int i = 0; i < 2; ++i) add((size_t)b * b * 8);    // qrX, qrY
   add((size_t)b * 8 * 2);         // tau, D
   for (int i = 0; i < 5; ++i) add((size_t)b * b * 8);    // Gram64, S64, Us64, Vs64, blk64
   add(householder_scratch_bytes(b));
@@ -177,7 +180,9 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.scal = (float*)ar.take(256);
   w.Y64 = (double*)ar.take((size_t)big * b * 8);
   w.W64 = (double*)ar.take((size_t)big * b * 8);
-  w.WS64 = (double*)ar.take((size_t)big * b * 8);
+  w.W2 = (double*)ar.take((size_t)big * b * 8);
+  w.qrX = (double*)ar.take((size_t)b * b * 8);
+  w.qrY = (double*)ar.take((size_t)b * b * 8);
   w.tau = (double*)ar.take((size_t)b * 8);
   w.D = (double*)ar.take((size_t)b * 8);
   w.Gram64 = (double*)ar.take((size_t)b * b * 8);
@@ -254,6 +259,43 @@ int mixed_apply_transposed(MCtx& c, const Planes& Xt, int64_t k, int64_t r, int6
   return 0;
 }
 
+// Householder QR (FP64) of the panel P (r x bi, ld r) into W64 (ld r) and
+// tau.  Panels of more than 128 columns are factored in two halves: the QR
+// of the first h = 128 columns, their block reflector applied to the rest,
+// P2 <- (I - W1 S1 W1^T)^T P2 (FP64 products, S1 from the FP64 Gram of W1),
+// and the QR of P2 below row h.  The reflectors are those of the unblocked
+// factorization (up to rounding order); each half keeps its rows in shared
+// memory where the whole panel would not fit, and its columns see at most
+// 127 trailing columns.
+int mixed_qr(MCtx& c, int64_t r, int64_t bi, double* P, int reserve) {
+  MixedWork& w = c.w;
+  constexpr int64_t h = 128;
+  if (bi <= h || r - h < bi - h)
+    return launch_householder_qr(r, bi, P, r, w.W64, w.tau, w.qr, c.status + 2, c.status, c.st,
+                                 reserve);
+  const int64_t h2 = bi - h;
+  RUTV_TRY(launch_householder_qr(r, h, P, r, w.W64, w.tau, w.qr, c.status + 2, c.status, c.st,
+                                 reserve));
+  RUTV_TRY(launch_dgemm(true, false, h, h, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, h, w.dgemm,
+                        w.dgemm_bytes, c.st));
+  RUTV_TRY(launch_wy_factor(h, w.Gram64, w.tau, w.S64, c.st));
+  double* P2 = P + h * r;
+  RUTV_TRY(launch_dgemm(true, false, h, h2, r, 1.0, w.W64, r, P2, r, 0.0, w.qrX, h, w.dgemm,
+                        w.dgemm_bytes, c.st));
+  RUTV_TRY(launch_dgemm(true, false, h, h2, h, 1.0, w.S64, h, w.qrX, h, 0.0, w.qrY, h, w.dgemm,
+                        w.dgemm_bytes, c.st));
+  RUTV_TRY(launch_dgemm(false, false, r, h2, h, -1.0, w.W64, r, w.qrY, h, 1.0, P2, r, w.dgemm,
+                        w.dgemm_bytes, c.st));
+  RUTV_TRY(launch_householder_qr(r - h, h2, P2 + h, r, w.W2, w.tau + h, w.qr, c.status + 2,
+                                 c.status, c.st, reserve));
+  // W(:, h:) = [0; W2]
+  double* Wr = w.W64 + h * r;
+  RUTV_CK(cudaMemset2DAsync(Wr, (size_t)r * 8, 0, (size_t)h * 8, (size_t)h2, c.st));
+  RUTV_CK(cudaMemcpy2DAsync(Wr + h, (size_t)r * 8, w.W2, (size_t)(r - h) * 8, (size_t)(r - h) * 8,
+                            (size_t)h2, cudaMemcpyDeviceToDevice, c.st));
+  return 0;
+}
+
 // Waits for the side stream's SVD and applies the pending row fold
 // T(blk, k+b:) <- Us^T T(blk, k+b:) on the main stream.
 int mixed_flush_fold(MCtx& c) {
@@ -287,8 +329,7 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
                             (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st, c.cap()));
     }
     RUTV_TRY(f32_to_f64(w.Y, rn, rn, bi, w.Y64, rn, c.st));
-    RUTV_TRY(launch_householder_qr(rn, bi, w.Y64, rn, w.W64, w.tau, w.qr, c.status + 2, c.status,
-                                   c.st, c.fold_pending ? kSvdSms : 0));
+    RUTV_TRY(mixed_qr(c, rn, bi, w.Y64, c.fold_pending ? kSvdSms : 0));
     RUTV_TRY(mixed_wy(c, rn, bi));
     RUTV_TRY(mixed_flush_fold(c));
     // X = T(:, k:) W (m x bi), then T(:, k:) -= X WS^T with X^T as planes
@@ -302,8 +343,7 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
   // ---------------- left transform
   if (rm > bi) {
     RUTV_TRY(merge_f64(w.T, k, k, rm, bi, 0, w.Y64, rm, c.st));
-    RUTV_TRY(launch_householder_qr(rm, bi, w.Y64, rm, w.W64, w.tau, w.qr, c.status + 2, c.status,
-                                   c.st));
+    RUTV_TRY(mixed_qr(c, rm, bi, w.Y64, 0));
     RUTV_TRY(split_f64(w.Y64, rm, rm, bi, 0, w.T, k, k, c.st));  // R and exact zeros
     RUTV_TRY(mixed_wy(c, rm, bi));
     if (rn > bi) {
