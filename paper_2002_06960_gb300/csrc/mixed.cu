@@ -12,6 +12,9 @@
 //     b x b SVD: FP64, the same kernels as the FP64 path.
 #include <cuda_bf16.h>
 
+#include <utility>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "mixed.h"
@@ -102,7 +105,8 @@ BgemmOut out_planes(const Planes& P, int64_t r0, int64_t c0, float alpha) {
 
 struct MixedWork {
   Planes T, Ut, Vt;             // m x n, m x m (U^T), n x n (V^T)
-  Planes W, WSt, Xp, Sp, Us, Vs; // small operands as planes
+  Planes W, WSt, Xp, Sp, Vs;     // small operands as planes
+  Planes UsAll;                 // U_s of every block step, b x (steps b), kept for the row folds
   __nv_bfloat16 *G, *Yb;        // BF16 sketch operands
   float *Y, *Z, *X, *tmp, *scal;
   double *Y64, *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64;
@@ -130,6 +134,20 @@ Planes carve_planes(Arena& ar, int64_t rows, int64_t cols) {
   return P;
 }
 
+int64_t nsteps(int64_t m, int64_t n, int64_t b) {
+  const int64_t p = m < n ? m : n;
+  return (p + b - 1) / b;
+}
+
+// Columns [c0, c0 + cols) of P as planes of their own (the base moves by
+// c0 ld elements, a multiple of 16 bytes since ld is a multiple of 8).
+Planes plane_cols(const Planes& P, int64_t c0, int64_t cols) {
+  Planes V = P;
+  for (int i = 0; i < 3; ++i) V.p[i] = P.p[i] + c0 * P.ld;
+  V.cols = cols;
+  return V;
+}
+
 size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   const int64_t big = m > n ? m : n;
   size_t s = 0;
@@ -141,7 +159,7 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add(planes_bytes(b, big));      // WSt
   add(planes_bytes(b, big));      // Xp (X^T or Xv/Xl)
   add(planes_bytes(b, b));        // Sp (S^T)
-  add(planes_bytes(b, b));        // Us
+  add(planes_bytes(b, nsteps(m, n, b) * b));  // UsAll
   add(planes_bytes(b, b));        // Vs
   add((size_t)pad8(big) * b * 2); // G
   add((size_t)pad8(big) * b * 2); // Yb
@@ -169,7 +187,7 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.WSt = carve_planes(ar, b, big);
   w.Xp = carve_planes(ar, b, big);
   w.Sp = carve_planes(ar, b, b);
-  w.Us = carve_planes(ar, b, b);
+  w.UsAll = carve_planes(ar, b, nsteps(m, n, b) * b);
   w.Vs = carve_planes(ar, b, b);
   w.G = (__nv_bfloat16*)ar.take((size_t)pad8(big) * b * 2);
   w.Yb = (__nv_bfloat16*)ar.take((size_t)pad8(big) * b * 2);
@@ -207,15 +225,20 @@ struct MCtx {
   MixedWork w;
   unsigned* status;
   cudaStream_t st;
-  // The small SVD and its fold-back run on the side stream beside the next
-  // block step (see the FP64 driver for the ordering argument); the row fold
-  // T(blk, k+b:) <- Us^T T(blk, k+b:) is applied on the main stream before
-  // the next right update.  While an SVD may be running, the main stream's
-  // persistent kernels leave it kSvdSms SMs.
+  // The small SVD of each block and its column folds (T(0:k, blk) V_s,
+  // V(:, blk) V_s, U(:, blk) U_s) run on the side stream beside the later
+  // block steps.  The row fold T(blk, k+b:) <- U_s^T T(blk, k+b:) is a left
+  // product on rows that no later step reads across: every later right
+  // update multiplies those rows from the right, which commutes with it, and
+  // every later left update, panel and sketch lies below them.  So all row
+  // folds wait until after the last step and then run on the main stream,
+  // and the main stream never waits for an SVD.  Once an SVD may be running,
+  // the main stream's persistent kernels leave it kSvdSms SMs.
   SideStream* side = nullptr;
-  bool fold_pending = false;
-  int64_t fold_k = 0, fold_bi = 0;
-  int cap() const { return fold_pending ? dev_info().sms - kSvdSms : 0; }
+  bool svd_live = false;
+  std::vector<std::pair<int64_t, int64_t>> folds;  // (k, bi) of each pending row fold
+  int reserve() const { return svd_live ? kSvdSms : 0; }
+  int cap() const { return svd_live ? dev_info().sms - kSvdSms : 0; }
 };
 
 // From the FP64 reflectors W64 (r x bi) and tau: W planes, S (FP64), and
@@ -251,11 +274,11 @@ int mixed_apply_transposed(MCtx& c, const Planes& Xt, int64_t k, int64_t r, int6
   const int64_t cols = Xt.cols;
   // Xv = W^T Xt(k:, :)   (bi x cols)
   RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, bi), opnd(Xt, 3, k, 0, 0), (int)bi, (int)cols, (int)r, 3,
-                        out_f32(w.X, bi), c.status, c.st));
+                        out_f32(w.X, bi), c.status, c.st, c.cap()));
   RUTV_TRY(split_f32(w.X, bi, bi, cols, 0, w.Xp, 0, 0, c.st));
   // Xt(k:, :) -= WS Xv   (A = WS via its transpose planes, K-major)
   RUTV_TRY(launch_bgemm(opnd(w.WSt, 3, 0, 0, 0, bi, r), opnd(w.Xp, 3, 0, 0, 0, bi, cols), (int)r, (int)cols,
-                        (int)bi, 3, out_planes(Xt, k, 0, -1.f), c.status, c.st));
+                        (int)bi, 3, out_planes(Xt, k, 0, -1.f), c.status, c.st, c.cap()));
   return 0;
 }
 
@@ -296,18 +319,21 @@ int mixed_qr(MCtx& c, int64_t r, int64_t bi, double* P, int reserve) {
   return 0;
 }
 
-// Waits for the side stream's SVD and applies the pending row fold
-// T(blk, k+b:) <- Us^T T(blk, k+b:) on the main stream.
-int mixed_flush_fold(MCtx& c) {
-  if (!c.fold_pending) return 0;
-  c.fold_pending = false;
+// Joins the side stream and applies the pending row folds
+// T(blk, k+b:) <- U_s^T T(blk, k+b:) on the main stream, in step order.
+int mixed_flush_folds(MCtx& c) {
+  if (!c.svd_live) return 0;
+  c.svd_live = false;
   RUTV_CK(cudaStreamWaitEvent(c.st, c.side->svd, 0));
   MixedWork& w = c.w;
-  const int64_t k = c.fold_k, bi = c.fold_bi, nc = c.n - k - bi;
-  if (nc <= 0) return 0;
-  RUTV_TRY(launch_bgemm(opnd(w.Us, 3, 0, 0, 0, bi, bi), opnd(w.T, 3, k, k + bi, 0), (int)bi, (int)nc,
-                        (int)bi, 3, out_f32(w.tmp, bi), c.status, c.st));
-  RUTV_TRY(split_f32(w.tmp, bi, bi, nc, 0, w.T, k, k + bi, c.st));
+  for (const auto& f : c.folds) {
+    const int64_t k = f.first, bi = f.second, nc = c.n - k - bi;
+    const Planes Us = plane_cols(w.UsAll, k, bi);
+    RUTV_TRY(launch_bgemm(opnd(Us, 3, 0, 0, 0, bi, bi), opnd(w.T, 3, k, k + bi, 0), (int)bi,
+                          (int)nc, (int)bi, 3, out_f32(w.tmp, bi), c.status, c.st));
+    RUTV_TRY(split_f32(w.tmp, bi, bi, nc, 0, w.T, k, k + bi, c.st));
+  }
+  c.folds.clear();
   return 0;
 }
 
@@ -329,42 +355,41 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
                             (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st, c.cap()));
     }
     RUTV_TRY(f32_to_f64(w.Y, rn, rn, bi, w.Y64, rn, c.st));
-    RUTV_TRY(mixed_qr(c, rn, bi, w.Y64, c.fold_pending ? kSvdSms : 0));
+    RUTV_TRY(mixed_qr(c, rn, bi, w.Y64, c.reserve()));
     RUTV_TRY(mixed_wy(c, rn, bi));
-    RUTV_TRY(mixed_flush_fold(c));
     // X = T(:, k:) W (m x bi), then T(:, k:) -= X WS^T with X^T as planes
     RUTV_TRY(launch_bgemm(opnd(w.T, 3, 0, k, 1), opnd(w.W, 3, 0, 0, 0, rn, bi), (int)m, (int)bi, (int)rn, 3,
-                          out_f32(w.X, m), c.status, c.st));
+                          out_f32(w.X, m), c.status, c.st, c.cap()));
     RUTV_TRY(split_f32(w.X, m, bi, m, 1, w.Xp, 0, 0, c.st));
     RUTV_TRY(launch_bgemm(opnd(w.Xp, 3, 0, 0, 0, bi, m), opnd(w.WSt, 3, 0, 0, 0, bi, rn), (int)m, (int)rn, (int)bi,
-                          3, out_planes(w.T, 0, k, -1.f), c.status, c.st));
+                          3, out_planes(w.T, 0, k, -1.f), c.status, c.st, c.cap()));
     if (c.want_v) RUTV_TRY(mixed_apply_transposed(c, w.Vt, k, rn, bi));
   }
   // ---------------- left transform
   if (rm > bi) {
     RUTV_TRY(merge_f64(w.T, k, k, rm, bi, 0, w.Y64, rm, c.st));
-    RUTV_TRY(mixed_qr(c, rm, bi, w.Y64, 0));
+    RUTV_TRY(mixed_qr(c, rm, bi, w.Y64, c.reserve()));
     RUTV_TRY(split_f64(w.Y64, rm, rm, bi, 0, w.T, k, k, c.st));  // R and exact zeros
     RUTV_TRY(mixed_wy(c, rm, bi));
     if (rn > bi) {
       const int64_t nc = rn - bi;
       RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, rm, bi), opnd(w.T, 3, k, k + bi, 0), (int)bi, (int)nc,
-                            (int)rm, 3, out_f32(w.X, bi), c.status, c.st));
+                            (int)rm, 3, out_f32(w.X, bi), c.status, c.st, c.cap()));
       RUTV_TRY(split_f32(w.X, bi, bi, nc, 0, w.Xp, 0, 0, c.st));
       RUTV_TRY(launch_bgemm(opnd(w.WSt, 3, 0, 0, 0, bi, rm), opnd(w.Xp, 3, 0, 0, 0, bi, nc), (int)rm, (int)nc,
-                            (int)bi, 3, out_planes(w.T, k, k + bi, -1.f), c.status, c.st));
+                            (int)bi, 3, out_planes(w.T, k, k + bi, -1.f), c.status, c.st, c.cap()));
     }
     if (c.want_u) RUTV_TRY(mixed_apply_transposed(c, w.Ut, k, rm, bi));
   }
   // ---------------- small SVD (FP64) and fold-back (six-product BF16), side stream
-  RUTV_TRY(mixed_flush_fold(c));  // the previous block's row fold precedes this SVD's folds
   cudaStream_t ss = c.side->st;
+  const Planes Us = plane_cols(w.UsAll, k, bi);
   RUTV_CK(cudaEventRecord(c.side->panel, c.st));
   RUTV_CK(cudaStreamWaitEvent(ss, c.side->panel, 0));
   RUTV_TRY(merge_f64(w.T, k, k, bi, bi, 0, w.blk64, bi, ss));
   RUTV_TRY(launch_small_svd((int)bi, w.blk64, bi, w.D, w.Us64, w.Vs64, c.status + 8, w.svd,
                             w.dgemm2, w.dgemm_bytes, ss));
-  RUTV_TRY(split_f64(w.Us64, bi, bi, bi, 0, w.Us, 0, 0, ss));
+  RUTV_TRY(split_f64(w.Us64, bi, bi, bi, 0, Us, 0, 0, ss));
   RUTV_TRY(split_f64(w.Vs64, bi, bi, bi, 0, w.Vs, 0, 0, ss));
   if (k > 0) {  // T(0:k, blk) <- T(0:k, blk) Vs
     RUTV_TRY(launch_bgemm(opnd(w.T, 3, 0, k, 1), opnd(w.Vs, 3, 0, 0, 0, bi, bi), (int)k, (int)bi, (int)bi, 3,
@@ -377,15 +402,14 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
     RUTV_TRY(split_f32(w.tmp2, bi, bi, n, 0, w.Vt, k, 0, ss));
   }
   if (c.want_u) {
-    RUTV_TRY(launch_bgemm(opnd(w.Us, 3, 0, 0, 0, bi, bi), opnd(w.Ut, 3, k, 0, 0), (int)bi, (int)m, (int)bi,
+    RUTV_TRY(launch_bgemm(opnd(Us, 3, 0, 0, 0, bi, bi), opnd(w.Ut, 3, k, 0, 0), (int)bi, (int)m, (int)bi,
                           3, out_f32(w.tmp2, bi), c.status, ss, kSvdSms));
     RUTV_TRY(split_f32(w.tmp2, bi, bi, m, 0, w.Ut, k, 0, ss));
   }
   RUTV_TRY(set_diag_planes(w.T, k, bi, w.D, ss));
   RUTV_CK(cudaEventRecord(c.side->svd, ss));
-  c.fold_pending = true;  // T(blk, k+bi:) <- Us^T T(blk, k+bi:) (empty when rn == bi)
-  c.fold_k = k;
-  c.fold_bi = bi;
+  c.svd_live = true;
+  if (rn > bi) c.folds.emplace_back(k, bi);  // T(blk, k+bi:) <- U_s^T T(blk, k+bi:)
   return 0;
 }
 
@@ -439,7 +463,7 @@ int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int 
     if (max_steps >= 0 && step >= max_steps) break;
     RUTV_TRY(mixed_step(c, step, k, bi));
   }
-  RUTV_TRY(mixed_flush_fold(c));  // also joins the side stream into the caller's stream
+  RUTV_TRY(mixed_flush_folds(c));  // also joins the side stream into the caller's stream
   RUTV_TRY(merge_f32(c.w.T, 0, 0, m, n, 0, T, m, st));
   if (c.want_u) RUTV_TRY(merge_f32(c.w.Ut, 0, 0, m, m, 1, U, m, st));
   if (c.want_v) RUTV_TRY(merge_f32(c.w.Vt, 0, 0, n, n, 1, V, n, st));

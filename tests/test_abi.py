@@ -65,3 +65,36 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(_lib, "_lib", None)
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.lib()
+
+
+def test_argument_errors_return_before_any_device_work(libpath):
+    """Each entry point validates its arguments on the host and returns the
+    documented negative code without touching the device (the pointer below
+    is never dereferenced, and no GPU is needed)."""
+    from paper_2002_06960_gb300 import _lib
+    L = _lib.lib()
+    p = 0x1000   # stands in for a device pointer; never read
+    # randutv_factor_ex: m, n, A, lda, b, q, T, first_step
+    assert L.randutv_factor_ex(0, 8, p, 8, 4, 1, 0, None, p, None, -1, None, 0) == -1
+    assert L.randutv_factor_ex(8, 0, p, 8, 4, 1, 0, None, p, None, -1, None, 0) == -2
+    assert L.randutv_factor_ex(8, 8, None, 8, 4, 1, 0, None, p, None, -1, None, 0) == -3
+    assert L.randutv_factor_ex(8, 8, p, 7, 4, 1, 0, None, p, None, -1, None, 0) == -4
+    assert L.randutv_factor_ex(8, 8, p, 8, 257, 1, 0, None, p, None, -1, None, 0) == -5
+    assert L.randutv_factor_ex(8, 8, p, 8, 4, 17, 0, None, p, None, -1, None, 0) == -6
+    assert L.randutv_factor_ex(8, 8, p, 8, 4, 1, 0, None, None, None, -1, None, 0) == -9
+    assert L.randutv_factor_ex(8, 8, p, 8, 4, 1, 0, None, p, None, -1, None, -1) == -13
+    # randutv_factor_mixed: b a multiple of 8 in [8, 256]
+    assert L.randutv_factor_mixed(64, 64, p, 64, 12, 1, 0, None, p, None, -1, None) == -5
+    assert L.randutv_factor_mixed(64, 64, p, 64, 264, 1, 0, None, p, None, -1, None) == -5
+    assert L.randutv_factor_mixed(64, 64, p, 64, 16, -1, 0, None, p, None, -1, None) == -6
+    assert L.randutv_factor_mixed(64, 64, p, 32, 16, 1, 0, None, p, None, -1, None) == -4
+    # randutv_lowrank / _backward: 1 <= k < min(m, n), b divides k
+    for k, b, q, code in [(40, 8, 1, -5), (0, 8, 1, -5), (24, 16, 1, -6), (16, 0, 1, -6),
+                          (16, 8, 17, -7)]:
+        assert L.randutv_lowrank(64, 40, p, 64, k, b, q, 0, p, None) == code
+        assert L.randutv_lowrank_backward(64, 40, p, 64, k, b, q, 0, p, p, None) == code
+    assert L.randutv_lowrank(64, 40, p, 64, 16, 8, 1, 0, None, None) == -9
+    assert L.randutv_lowrank_backward(64, 40, p, 64, 16, 8, 1, 0, p, None, None) == -10
+    # randutv_gemm_bf16: planes must be 1 or 3
+    assert L.randutv_gemm_bf16(b"N", 8, 8, 8, 1.0, p, 8, p, 8, 0.0, p, 8, 2, None) == -13
+    assert L.randutv_gemm_bf16(b"X", 8, 8, 8, 1.0, p, 8, p, 8, 0.0, p, 8, 1, None) == -1

@@ -110,3 +110,27 @@ def test_autotuner_installs_a_table(pkg):
     assert set(rep) == {0, 1}
     assert all(b in (16, 32, 64) and ms > 0 for b, ms in rep.values())
     batched.set_tuning([0] * batched.N_CLASSES)  # back to the default
+
+
+@pytest.mark.parametrize("b", [32, 64])
+def test_batched_maximum_sizes(pkg, b):
+    """Matrices at the 1024 limit, square and ragged, checked by properties
+    that hold at any size: reconstruction and orthogonality at the FP32
+    level, exact zeros below the diagonal, and the leading diagonal of T
+    against the prescribed spectrum."""
+    p, batched = pkg
+    sizes = [(1024, 1024), (1024, 1001), (999, 1024), (1024, 40)]
+    mats = _mats(p, sizes, seed=11)
+    plan = batched.BatchedPlan([d for _, d in mats], b=b, q=1, seed=3)
+    plan.run()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().sum()) == 0
+    for i, (A, _) in enumerate(mats):
+        U, T, V = (plan.U[i].cpu().double(), plan.T[i].cpu().double(), plan.V[i].cpu().double())
+        Aq = A.to(f32).double()
+        assert oracle.recon_error(Aq, U, T, V) < 2e-6, i
+        assert oracle.orth_error(U) < 2e-6 and oracle.orth_error(V) < 2e-6, i
+        assert float(torch.tril(T, -1).abs().max()) == 0.0
+        sig = torch.exp(-torch.arange(4, dtype=f64) / 16.0)
+        d = torch.diagonal(T)[:4].abs()
+        assert float(((d - sig).abs() / sig).max()) < 1e-3, (i, d)

@@ -76,7 +76,8 @@ def _mixed(pkg, A, b, q, seed):
 
 @pytest.mark.parametrize("kind,m,n,b,q", [("exp40", 512, 512, 64, 1), ("smooth", 1024, 1024, 256, 2),
                                           ("smooth", 768, 512, 128, 2), ("smooth", 512, 768, 128, 1),
-                                          ("gauss", 300, 260, 64, 1)])
+                                          ("gauss", 300, 260, 64, 1), ("exp40", 333, 517, 64, 1),
+                                          ("smooth", 517, 333, 128, 0)])
 def test_mixed_factorization_errors(pkg, kind, m, n, b, q):
     A = inputs.matrix(kind, m, n, seed=1)
     U, T, V = _mixed(pkg, A, b, q, 0)
@@ -107,3 +108,29 @@ def test_mixed_single_block_is_svd(pkg):
     A = inputs.prescribed(96, 96, sig, seed=2)
     U, T, V = _mixed(pkg, A, 128, 1, 0)
     assert torch.allclose(torch.diagonal(T), sig, rtol=1e-5, atol=1e-6)
+
+
+@pytest.mark.parametrize("m,n,b", [(100, 60, 64), (60, 100, 64), (37, 37, 40)])
+def test_mixed_one_ragged_block(pkg, m, n, b):
+    """b > min(m, n) with min(m, n) not a multiple of 8: one block of width
+    p = min(m, n).  T(0:p, 0:p) is the diagonal of the block's SVD.  For
+    m >= n the block is all of A, so that diagonal is A's spectrum to FP32
+    accuracy.  For m < n the block is A V1 with V1 from the BF16 sketch, whose
+    span holds A's row space only to the sketch's rounding: the diagonal then
+    lies below the spectrum (interlacing, A V1 being A times orthonormal
+    columns) and meets it at the top."""
+    A = inputs.matrix("exp16", m, n, seed=4)
+    U, T, V = _mixed(pkg, A, b, 1, 0)
+    p = min(m, n)
+    assert oracle.recon_error(A, U, T, V) < 2e-6
+    assert oracle.orth_error(U) < 2e-6 and oracle.orth_error(V) < 2e-6
+    assert float(torch.tril(T, -1).abs().max()) == 0.0
+    sig = torch.linalg.svdvals(A)
+    d = torch.diagonal(T)[:p].abs()
+    off = T[:p, :p] - torch.diag(torch.diagonal(T)[:p])
+    assert float(off.abs().max()) < 1e-5 * float(sig[0])
+    if m >= n:
+        assert torch.allclose(d, sig, rtol=1e-4, atol=1e-6 * float(sig[0])), (d - sig).abs().max()
+    else:
+        assert bool((d <= sig * (1 + 1e-5) + 1e-6 * float(sig[0])).all()), (d - sig).max()
+        assert float(((d[:4] - sig[:4]).abs() / sig[:4]).max()) < 1e-3, (d[:4], sig[:4])
