@@ -24,8 +24,13 @@ namespace {
 
 constexpr int BT = 256;          // threads per CTA
 constexpr int BMAX = 64;         // largest block size of the batched path
-constexpr int GT = 64, GK = 32;  // CTA GEMM tile (GT x GT outputs, GK deep per stage)
-constexpr int GLD = GT + 1;      // row stride of the tiles in shared memory (conflict-free)
+constexpr int GK = 32;           // depth of one CTA GEMM stage
+constexpr int GSTAGES = 3;       // CTA GEMM pipeline depth
+constexpr int GBUF = GSTAGES * GK * (129 + 33);  // floats of the GEMM operand buffers
+constexpr int GCBUF = GSTAGES * 4096;            // floats of the GEMM C-tile buffers
+// Below S (which sits at the top of the shared union): room to stage W for
+// the WY factor
+constexpr int WY_SMEM_FLOATS = GBUF + GCBUF - 2 * BMAX * (BMAX + 1);
 constexpr int NWARP = BT / 32;
 
 struct BatchDesc {
@@ -54,17 +59,20 @@ struct Smem {
   // The GEMM tiles and the WY / SVD arrays are never live at the same time.
   union {
     struct {
-      float gA[2][GK][GLD];  // A tile, k-major: gA[buf][k][m]
-      float gB[2][GK][GLD];  // B tile, k-major: gB[buf][k][n]
+      float gbuf[GBUF];   // GEMM operands, k-major: A [GSTAGES][GK][TM+1], then B [GSTAGES][GK][TN+1]
+      float gcbuf[GCBUF]; // C tiles for beta != 0: [GSTAGES][TN][TM]
     };
     struct {
       float svB[BMAX][BMAX + 1];  // column j at svB[j][i]
       float svV[BMAX][BMAX + 1];
+      float svpad[WY_SMEM_FLOATS - 2 * BMAX * (BMAX + 1)];
       double S[BMAX][BMAX + 1];   // S(i, j) at S[j][i], FP64
     };
   };
   double tau[BMAX];
   float wv[BMAX];
+  float qscale[BMAX];  // panel QR: 1 / (alpha - beta) of each reflector
+  float qbeta[BMAX];   // panel QR: R(j, j)
   float D[BMAX];
   float vbest[BMAX];
   int rankof[BMAX];
@@ -74,94 +82,135 @@ struct Smem {
 };
 
 // ------------------------------------------------------------ CTA GEMM
+// 4-byte asynchronous copy global -> shared (zero fill when !valid), and the
+// group commit / wait of the copies a thread has issued.
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
 // C = alpha op(A) op(B) + beta C (FP32, column-major); C must not alias A, B.
-// 64 x 64 output tiles, 4 x 4 per thread (rows tx + 16 i, columns ty + 16 j),
-// K in stages of 32 through two shared-memory buffers: the global loads of
-// stage s + 1 are in flight (held in registers) while stage s is multiplied.
-template <bool TA, bool TB>
-__device__ void cta_gemm(int M, int N, int K, float alpha, const float* __restrict__ A, int64_t lda,
-                         const float* __restrict__ B, int64_t ldb, float beta, float* C,
-                         int64_t ldc, Smem& sm) {
-  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
-  constexpr int PER = GT * GK / BT;  // elements of each tile a thread loads per stage
-  for (int m0 = 0; m0 < M; m0 += GT) {
-    for (int n0 = 0; n0 < N; n0 += GT) {
-      float acc[4][4];
+// TM x TN output tiles (TM TN = 4096), 4 x 4 per thread: rows tx + (TM/4) i,
+// columns ty + (TN/4) j.  K goes in stages of GK, and the stages of all tiles
+// form one pipeline through GSTAGES shared-memory buffers filled by
+// asynchronous copies: stage s is multiplied while stages s + 1 and s + 2
+// (of this tile or the next ones) are in flight, and with beta != 0 the copy
+// of a tile's C travels with its last stage.  Every output is one FMA chain over k = 0 .. K-1 in
+// order, whatever the tile shape, so the result does not depend on it.
+template <bool TA, bool TB, int TM, int TN>
+__device__ void cta_gemm_t(int M, int N, int K, float alpha, const float* __restrict__ A,
+                           int64_t lda, const float* __restrict__ B, int64_t ldb, float beta,
+                           float* C, int64_t ldc, Smem& sm) {
+  static_assert(TM * TN == 16 * BT, "4 x 4 outputs per thread");
+  constexpr int RX = TM / 4, RY = TN / 4;
+  constexpr int PA = TM * GK / BT, PB = TN * GK / BT;  // elements per thread per stage
+  static_assert(GSTAGES * GK * (TM + 1) + GSTAGES * GK * (TN + 1) <= GBUF, "tile buffers fit");
+  float(*gA)[GK][TM + 1] = reinterpret_cast<float(*)[GK][TM + 1]>(sm.gbuf);
+  float(*gB)[GK][TN + 1] =
+      reinterpret_cast<float(*)[GK][TN + 1]>(sm.gbuf + GSTAGES * GK * (TM + 1));
+  const int tid = threadIdx.x, tx = tid % RX, ty = tid / RX;
+  const int tiles_m = (M + TM - 1) / TM, tiles_n = (N + TN - 1) / TN, nk = (K + GK - 1) / GK;
+  const int total = tiles_m * tiles_n * nk;
+  // element e = tid + BT t of a tile; the fast index follows the contiguous
+  // direction of the source, so the global reads coalesce
+  auto issue = [&](int s) {
+    if (s < total) {
+      const int buf = s % GSTAGES;
+      const int tile = s / nk, k0 = (s - tile * nk) * GK;
+      const int m0 = (tile % tiles_m) * TM, n0 = (tile / tiles_m) * TN;
+#pragma unroll
+      for (int t = 0; t < PA; ++t) {
+        const int e = tid + BT * t;
+        int mm, kk;
+        if (!TA) { mm = e % TM; kk = e / TM; } else { kk = e % GK; mm = e / GK; }
+        const int gm = m0 + mm, gk = k0 + kk;
+        const bool v = gm < M && gk < K;
+        cp_async4(&gA[buf][kk][mm], v ? (TA ? A + gk + (int64_t)gm * lda : A + gm + (int64_t)gk * lda) : A, v);
+      }
+#pragma unroll
+      for (int t = 0; t < PB; ++t) {
+        const int e = tid + BT * t;
+        int nn, kb;
+        if (!TB) { kb = e % GK; nn = e / GK; } else { nn = e % TN; kb = e / TN; }
+        const int gn = n0 + nn, gkb = k0 + kb;
+        const bool v = gn < N && gkb < K;
+        cp_async4(&gB[buf][kb][nn], v ? (TB ? B + gn + (int64_t)gkb * ldb : B + gkb + (int64_t)gn * ldb) : B, v);
+      }
+      if (beta != 0.f && k0 + GK >= K) {
+        float* gC = sm.gcbuf + buf * 4096;
+#pragma unroll 4
+        for (int t = 0; t < 4096 / BT; ++t) {
+          const int e = tid + BT * t, mm = e % TM, nn = e / TM;
+          const int gm = m0 + mm, gn = n0 + nn;
+          const bool v = gm < M && gn < N;
+          cp_async4(gC + e, v ? C + gm + (int64_t)gn * ldc : C, v);
+        }
+      }
+    }
+    cp_async_commit();  // one group per stage index, empty past the end
+  };
+  issue(0);
+  issue(1);
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  for (int s = 0; s < total; ++s) {
+    cp_async_wait<1>();  // this thread's copies of stage s have landed
+    __syncthreads();     // everyone's have; and stage s - 1 is no longer read
+    issue(s + 2);        // into the buffer of stage s - 1
+    const int buf = s % GSTAGES;
+    const int tile = s / nk;
+    const bool last = s - tile * nk == nk - 1;
+    const int m0 = (tile % tiles_m) * TM, n0 = (tile / tiles_m) * TN;
+#pragma unroll 8
+    for (int k = 0; k < GK; ++k) {
+      float a[4], bb[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = gA[buf][k][tx + RX * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bb[j] = gB[buf][k][ty + RY * j];
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-      float ra[PER], rb[PER];
-      // element e = tid + BT t of a tile; the fast index follows the
-      // contiguous direction of the source, so the global loads coalesce
-      auto load = [&](int k0) {
-#pragma unroll
-        for (int t = 0; t < PER; ++t) {
-          const int e = tid + BT * t;
-          int mm, kk;
-          if (!TA) { mm = e % GT; kk = e / GT; } else { kk = e % GK; mm = e / GK; }
-          const int gm = m0 + mm, gk = k0 + kk;
-          ra[t] = (gm < M && gk < K) ? (TA ? A[gk + (int64_t)gm * lda] : A[gm + (int64_t)gk * lda])
-                                     : 0.f;
-          int nn, kb;
-          if (!TB) { kb = e % GK; nn = e / GK; } else { nn = e % GT; kb = e / GT; }
-          const int gn = n0 + nn, gkb = k0 + kb;
-          rb[t] = (gn < N && gkb < K) ? (TB ? B[gn + (int64_t)gkb * ldb] : B[gkb + (int64_t)gn * ldb])
-                                      : 0.f;
-        }
-      };
-      auto store = [&](int buf) {
-#pragma unroll
-        for (int t = 0; t < PER; ++t) {
-          const int e = tid + BT * t;
-          int mm, kk;
-          if (!TA) { mm = e % GT; kk = e / GT; } else { kk = e % GK; mm = e / GK; }
-          sm.gA[buf][kk][mm] = ra[t];
-          int nn, kb;
-          if (!TB) { kb = e % GK; nn = e / GK; } else { nn = e % GT; kb = e / GT; }
-          sm.gB[buf][kb][nn] = rb[t];
-        }
-      };
-      load(0);
-      store(0);
-      __syncthreads();
-      int buf = 0;
-      for (int k0 = 0; k0 < K; k0 += GK) {
-        const bool more = k0 + GK < K;
-        if (more) load(k0 + GK);
-#pragma unroll 8
-        for (int k = 0; k < GK; ++k) {
-          float a[4], bb[4];
-#pragma unroll
-          for (int i = 0; i < 4; ++i) a[i] = sm.gA[buf][k][tx + 16 * i];
-#pragma unroll
-          for (int j = 0; j < 4; ++j) bb[j] = sm.gB[buf][k][ty + 16 * j];
-#pragma unroll
-          for (int i = 0; i < 4; ++i)
-#pragma unroll
-            for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
-        }
-        if (more) store(buf ^ 1);  // the other buffer was released by the last barrier
-        __syncthreads();
-        buf ^= 1;
-      }
+        for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(a[i], bb[j], acc[i][j]);
+    }
+    if (last) {
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const int n = n0 + ty + 16 * j;
-        if (n >= N) continue;
+        const int n = n0 + ty + RY * j;
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-          const int m = m0 + tx + 16 * i;
-          if (m >= M) continue;
-          float* c = C + m + (int64_t)n * ldc;
+          const int m = m0 + tx + RX * i;
           float v = alpha * acc[i][j];
-          if (beta != 0.f) v = fmaf(beta, *c, v);
-          *c = v;
+          if (beta != 0.f) v = fmaf(beta, sm.gcbuf[buf * 4096 + (ty + RY * j) * TM + tx + RX * i], v);
+          if (m < M && n < N) C[m + (int64_t)n * ldc] = v;
+          acc[i][j] = 0.f;
         }
       }
     }
   }
+  cp_async_wait<0>();
   __syncthreads();
+}
+
+// Tile shape by the output's shape: a narrow side of at most 32 gets the
+// 128 x 32 (or 32 x 128) tile instead of half-empty 64 x 64 tiles.
+template <bool TA, bool TB>
+__device__ void cta_gemm(int M, int N, int K, float alpha, const float* __restrict__ A, int64_t lda,
+                         const float* __restrict__ B, int64_t ldb, float beta, float* C,
+                         int64_t ldc, Smem& sm) {
+  if (N <= 32)
+    cta_gemm_t<TA, TB, 128, 32>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+  else if (M <= 32)
+    cta_gemm_t<TA, TB, 32, 128>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
+  else
+    cta_gemm_t<TA, TB, 64, 64>(M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, sm);
 }
 
 __device__ void cta_copy(int rows, int cols, const float* src, int64_t lds, float* dst,
@@ -252,6 +301,86 @@ __device__ void cta_householder(int r, int c, float* Pn, int64_t ldp, float* W, 
     }
     __syncthreads();
   }
+}
+
+// The same factorization with the panel held in shared memory (in the GEMM
+// buffers, which are idle here) when r c fits: one read and one write of the
+// panel instead of three passes over it per column.  The arithmetic and its
+// order are those of cta_householder, so the two give identical bits.
+constexpr int QR_SMEM_FLOATS = GBUF + GCBUF;
+__device__ void cta_householder_smem(int r, int c, float* Pn, int64_t ldp, float* W, Smem& sm) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float* P = sm.gbuf;  // column l at P[l * r], contiguous with gcbuf
+  for (int64_t e = tid; e < (int64_t)r * c; e += BT) {
+    const int i = (int)(e % r), l = (int)(e / r);
+    P[e] = Pn[i + (int64_t)l * ldp];
+  }
+  __syncthreads();
+  for (int j = 0; j < c; ++j) {
+    const float* pj = P + (int64_t)j * r;
+    double ss = 0.0;
+    for (int i = j + 1 + tid; i < r; i += BT) {
+      const double x = pj[i];
+      ss = fma(x, x, ss);
+    }
+    ss = cta_sum(ss, sm);
+    if (tid == 0) {
+      const double alpha = pj[j];
+      double tau, beta, scale;
+      if (ss == 0.0) {
+        tau = 0.0; beta = alpha; scale = 0.0;
+      } else {
+        const double nrm = sqrt(fma(alpha, alpha, ss));
+        beta = (alpha >= 0.0) ? -nrm : nrm;
+        tau = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      sm.tau[j] = tau;
+      sm.qscale[j] = (float)scale;
+      sm.qbeta[j] = (float)beta;
+    }
+    __syncthreads();
+    const double tau = sm.tau[j];
+    const float scale = sm.qscale[j];
+    // Each warp takes whole columns l > j: the dot w_j^T p_l (every lane ends
+    // with the same sum) and then p_l -= w_j (tau w_j^T p_l) on its own.
+    if (tau != 0.0) {
+      for (int l = j + 1 + warp; l < c; l += NWARP) {
+        float* pl = P + (int64_t)l * r;
+        float d = 0.f;
+        for (int i = j + lane; i < r; i += 32) {
+          const float v = (i == j) ? 1.f : pj[i] * scale;
+          d = fmaf(v, pl[i], d);
+        }
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        const float wl = (float)(tau * (double)d);
+        for (int i = j + lane; i < r; i += 32) {
+          const float v = (i == j) ? 1.f : pj[i] * scale;
+          pl[i] = fmaf(-v, wl, pl[i]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+  // R (with exact zeros below the diagonal) back to the panel; W explicit
+  for (int64_t e = tid; e < (int64_t)r * c; e += BT) {
+    const int i = (int)(e % r), l = (int)(e / r);
+    const float x = P[e];
+    float w, y;
+    if (i < l) { w = 0.f; y = x; }
+    else if (i == l) { w = 1.f; y = sm.qbeta[l]; }
+    else { w = (sm.tau[l] != 0.0) ? x * sm.qscale[l] : 0.f; y = 0.f; }
+    W[i + (int64_t)l * r] = w;
+    Pn[i + (int64_t)l * ldp] = y;
+  }
+  __syncthreads();
+}
+
+__device__ void cta_qr(int r, int c, float* Pn, int64_t ldp, float* W, Smem& sm) {
+  if ((int64_t)r * c <= QR_SMEM_FLOATS)
+    cta_householder_smem(r, c, Pn, ldp, W, sm);
+  else
+    cta_householder(r, c, Pn, ldp, W, sm);
 }
 
 // Error-free transformation of a sum: s + e == a + b exactly (Knuth's two-sum).
@@ -578,15 +707,22 @@ __device__ void cta_sketch(uint64_t seed, int step, int mid, int rows, int cols,
   __syncthreads();
 }
 
-// W (r x bi) and sm.tau -> sm.S and WS = W S^T (r x bi).
+// W (r x bi) and sm.tau -> sm.S and WS = W S^T (r x bi).  W is read from a
+// shared-memory copy when it fits below S (the same arithmetic either way).
 __device__ void cta_wy_ws(int r, int bi, Work& w, Smem& sm) {
-  cta_gram64(r, bi, w.W, w.Gm);
+  const float* W = w.W;
+  if ((int64_t)r * bi <= WY_SMEM_FLOATS) {
+    for (int64_t e = threadIdx.x; e < (int64_t)r * bi; e += BT) sm.gbuf[e] = w.W[e];
+    __syncthreads();
+    W = sm.gbuf;
+  }
+  cta_gram64(r, bi, W, w.Gm);
   cta_wy(bi, w.Gm, sm);
   // WS = W S^T with S in shared memory: S^T(l, j) = S(j, l) = sm.S[l][j]
   for (int64_t e = threadIdx.x; e < (int64_t)r * bi; e += BT) {
     const int i = (int)(e % r), j = (int)(e / r);
     float s = 0.f;
-    for (int l = j; l < bi; ++l) s = fmaf(w.W[i + (int64_t)l * r], (float)sm.S[l][j], s);
+    for (int l = j; l < bi; ++l) s = fmaf(W[i + (int64_t)l * r], (float)sm.S[l][j], s);
     w.WS[i + (int64_t)j * r] = s;
   }
   __syncthreads();
@@ -618,7 +754,7 @@ __device__ int factor_one(const BatchDesc& d, uint64_t seed, Work& w, Smem& sm) 
         cta_gemm<false, false>(rm, bi, rn, 1.f, T22, ldt, w.Y, rn, 0.f, w.Z, rm, sm);
         cta_gemm<true, false>(rn, bi, rm, 1.f, T22, ldt, w.Z, rm, 0.f, w.Y, rn, sm);
       }
-      cta_householder(rn, bi, w.Y, rn, w.W, sm);
+      cta_qr(rn, bi, w.Y, rn, w.W, sm);
       cta_wy_ws(rn, bi, w, sm);
       float* Tk = T + (int64_t)k * ldt;
       cta_gemm<false, false>(m, bi, rn, 1.f, Tk, ldt, w.W, rn, 0.f, w.X, m, sm);
@@ -630,7 +766,7 @@ __device__ int factor_one(const BatchDesc& d, uint64_t seed, Work& w, Smem& sm) 
       }
     }
     if (rm > bi) {
-      cta_householder(rm, bi, T22, ldt, w.W, sm);
+      cta_qr(rm, bi, T22, ldt, w.W, sm);
       cta_wy_ws(rm, bi, w, sm);
       if (rn > bi) {
         const int nc = rn - bi;
