@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched line (4096 matrices of sizes in [64, 1024])")
     ap.add_argument("--batched-count", type=int, default=4096)
+    ap.add_argument("--no-ooc", action="store_true",
+                    help="skip the out-of-HBM form (T, U, V in host memory)")
     ap.add_argument("--no-backward", action="store_true",
                     help="skip the rank-k backward line (4096^2, k=256, b=128)")
     return ap.parse_args()
@@ -289,6 +291,57 @@ def run_ours(args, world, rank, local):
         "clocks": clk,
     }
     return out, A_host
+
+
+# ------------------------------------------------------------ out of HBM
+
+def run_ooc(args, A_host, fp64_ms=None, device_gib=1.0):
+    """Out-of-HBM form: T (in place of A), U and V in pinned host memory,
+    streamed through a device budget of `device_gib` GiB (the matrix alone is
+    8 n^2 bytes).  Timed on the host around the synchronous call: the data
+    start and end in host memory, so this is also its end-to-end number."""
+    import paper_2002_06960_gb300 as pkg
+
+    n, b, q = args.n, args.b, args.q
+    flops = inputs.algorithmic_flops(n, n, b, q)
+    budget = max(int(device_gib * 2 ** 30), pkg.randutv_ooc_min_device_bytes(n, n, b))
+    # warm-up on a small case (streams, events, workspace)
+    Ws = pkg.colmajor_empty(1024, 1024, device="cpu", pin=True)
+    Ws.copy_(inputs.gaussian(1024, 1024, 2))
+    pkg.randutv_factor_ooc(Ws, b, q, 0, None, None)
+    T = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    U = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    V = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    T.copy_(A_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    moved = pkg.randutv_factor_ooc(T, b, q, 0, U, V, device_bytes=budget)
+    secs = time.perf_counter() - t0
+    # sampled errors, on the device
+    g = torch.Generator().manual_seed(0)
+    rows = torch.randperm(n, generator=g)[:64]
+    Td, Vd = T.cuda(), V.cuda()
+    rec = (U[rows, :].cuda() @ Td) @ Vd.T
+    Ar = A_host[rows, :].cuda()
+    recon = float(torch.linalg.norm(rec - Ar) / torch.linalg.norm(Ar))
+    cols = torch.randperm(n, generator=g)[:64].cuda()
+    eye = torch.zeros(n, 64, dtype=torch.float64, device="cuda")
+    eye[cols, torch.arange(64, device="cuda")] = 1.0
+    orth_v = float(torch.linalg.norm(Vd.T @ Vd[:, cols] - eye) / 8.0)
+    del Td, Vd
+    out = {
+        "workload": f"randutv_ooc_fp64_n{n}_b{b}_q{q}",
+        "value": round(flops / secs / 1e12, 4), "unit": "TFLOP/s", "seconds": round(secs, 3),
+        "dtype": "f64",
+        "data": "T, U, V in pinned host memory; device budget "
+                f"{budget / 2 ** 30:.2f} GiB against {3 * 8 * n * n / 2 ** 30:.1f} GiB of T, U, V",
+        "host_device_bytes": moved,
+        "host_link_GBps": round(moved / secs / 1e9, 1),
+        "errors": {"recon_sampled_rows": recon, "orth_v_sampled": orth_v},
+    }
+    if fp64_ms:
+        out["time_vs_in_hbm"] = round(secs / (fp64_ms * 1e-3), 3)
+    return out
 
 
 # ------------------------------------------------------- mixed precision
@@ -631,6 +684,11 @@ def main():
             print(json.dumps(out), flush=True)
         return
     out, A_host = run_ours(args, world, rank, local)
+    if world == 1 and not args.no_ooc:
+        try:
+            out["out_of_hbm"] = run_ooc(args, A_host, fp64_ms=out["ms_per_step"])
+        except Exception as e:  # report, never hide
+            out["out_of_hbm"] = {"error": repr(e)}
     if not args.no_mixed and args.n >= 1024:
         try:
             out["mixed"] = [run_mixed(args, args.n, args.n, 256, 2, args.mixed_steps, 3,

@@ -145,6 +145,31 @@ int randutv_factor_batched(int batch, const int64_t* m, const int64_t* n, const 
  * and CTAs per SM for the persistent grid (0 = occupancy limit). */
 int randutv_batched_set_tuning(const int* b_for_class, int nclasses, int ctas_per_sm);
 
+/* ------------------------------------------------------------- out of HBM --
+ * The factorization of a matrix that stays in HOST memory (§3.2: the
+ * out-of-core setting, here the device's HBM against the host's memory).
+ * The same block steps in FP64 as randutv_factor; every pass over a trailing
+ * region streams it through the device in panels, with the copies in and out
+ * overlapping the arithmetic (two copy streams, three panel buffers).
+ *   A (3)      HOST, m x n with lda (4) >= m; overwritten by T.  Pinned
+ *              memory (cudaHostAlloc / cudaHostRegister) lets the copies run
+ *              asynchronously; pageable memory works, without the overlap.
+ *   U (8), V (9)  HOST, m x m (ld m) and n x n (ld n), or NULL.
+ *   device_bytes (10)  device memory the call may use (workspace and panel
+ *              buffers): at least randutv_ooc_min_device_bytes(m, n, b);
+ *              larger panels cost fewer copies per pass.
+ *   bytes_moved (11)   HOST, optional: the bytes copied between host and
+ *              device by the call.
+ *   b, q, seed as in randutv_factor; stream (12): the compute stream.
+ * Synchronous: returns after the factorization (0, a device status, or -i).
+ * The result is deterministic for a given device_bytes; against
+ * randutv_factor (and between budgets) it differs only in rounding, since the
+ * panel cut changes the summation order of some products. */
+size_t randutv_ooc_min_device_bytes(int64_t m, int64_t n, int b);
+int randutv_factor_ooc(int64_t m, int64_t n, double* A, int64_t lda, int b, int q, uint64_t seed,
+                       double* U, double* V, size_t device_bytes, double* bytes_moved,
+                       void* stream);
+
 /* ---------------------------------------------------- low rank and adjoint --
  * A_k = U(:, 0:k) U(:, 0:k)^T A, the rank-k approximation of §1.1
  * (A_k = U(:,1:k) R(1:k,:) V^*), through the first k/b block steps of §3.1

@@ -56,6 +56,9 @@ _SIGS = {
     "randutv_factor_batched": (c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_u64, c_vp,
                                        c_vp, c_vp, c_vp, c_vp]),
     "randutv_batched_set_tuning": (c_int, [c_vp, c_int, c_int]),
+    "randutv_ooc_min_device_bytes": (ctypes.c_size_t, [c_i64, c_i64, c_int]),
+    "randutv_factor_ooc": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_u64, c_vp, c_vp,
+                                   ctypes.c_size_t, c_vp, c_vp]),
     "randutv_lowrank": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64, c_vp, c_vp]),
     "randutv_lowrank_backward": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64,
                                          c_vp, c_vp, c_vp]),
@@ -196,6 +199,34 @@ def randutv_factor_host(A_host, b, q, seed, U_host=None, T_host=None, V_host=Non
     _check("randutv_factor_host", lib().randutv_factor_host(
         m, n, _ptr(A_host), lda, b, q, seed, _ptr(U_host), _ptr(T_host), _ptr(V_host)))
     return U_host, T_host, V_host
+
+
+def randutv_ooc_min_device_bytes(m, n, b):
+    return int(lib().randutv_ooc_min_device_bytes(m, n, b))
+
+
+def randutv_factor_ooc(A_host, b, q, seed, U_host=None, V_host=None, device_bytes=0):
+    """Out-of-HBM randUTV: A_host (CPU float64 column-major, pinned for the
+    copies to overlap) is overwritten by T; U_host, V_host (CPU, or None) get
+    U and V.  device_bytes = 0 takes twice the minimum.  Returns the bytes
+    copied between host and device."""
+    m, n = A_host.shape
+    if A_host.is_cuda:
+        raise ValueError("A_host must be a CPU tensor")
+    lda = _colmajor(A_host, m, n, "A_host")
+    for t, r, c, nm in ((U_host, m, m, "U_host"), (V_host, n, n, "V_host")):
+        if t is not None:
+            if t.is_cuda or t.dtype != torch.float64:
+                raise ValueError(f"{nm} must be a CPU float64 tensor")
+            if _colmajor(t, r, c, nm) != r:
+                raise ValueError(f"{nm} must have leading dimension {r}")
+    if device_bytes <= 0:
+        device_bytes = 2 * randutv_ooc_min_device_bytes(m, n, b)
+    moved = ctypes.c_double(0.0)
+    _check("randutv_factor_ooc", lib().randutv_factor_ooc(
+        m, n, _ptr(A_host), lda, b, q, seed, _ptr(U_host), _ptr(V_host), device_bytes,
+        ctypes.byref(moved), _stream()))
+    return moved.value
 
 
 def randutv_philox_normal(seed, step, matrix_id, stream_id, rows, cols, device="cuda"):

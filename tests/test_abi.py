@@ -95,6 +95,15 @@ def test_argument_errors_return_before_any_device_work(libpath):
         assert L.randutv_lowrank_backward(64, 40, p, 64, k, b, q, 0, p, p, None) == code
     assert L.randutv_lowrank(64, 40, p, 64, 16, 8, 1, 0, None, None) == -9
     assert L.randutv_lowrank_backward(64, 40, p, 64, 16, 8, 1, 0, p, None, None) == -10
+    # randutv_factor_ooc: host A, the device budget at least the minimum
+    need = L.randutv_ooc_min_device_bytes(64, 40, 8)
+    assert need > 0 and L.randutv_ooc_min_device_bytes(0, 40, 8) == 0
+    assert L.randutv_factor_ooc(0, 40, p, 64, 8, 1, 0, None, None, need, None, None) == -1
+    assert L.randutv_factor_ooc(64, 40, None, 64, 8, 1, 0, None, None, need, None, None) == -3
+    assert L.randutv_factor_ooc(64, 40, p, 63, 8, 1, 0, None, None, need, None, None) == -4
+    assert L.randutv_factor_ooc(64, 40, p, 64, 300, 1, 0, None, None, need, None, None) == -5
+    assert L.randutv_factor_ooc(64, 40, p, 64, 8, 17, 0, None, None, need, None, None) == -6
+    assert L.randutv_factor_ooc(64, 40, p, 64, 8, 1, 0, None, None, need - 1, None, None) == -10
     # randutv_gemm_bf16: planes must be 1 or 3
     assert L.randutv_gemm_bf16(b"N", 8, 8, 8, 1.0, p, 8, p, 8, 0.0, p, 8, 2, None) == -13
     assert L.randutv_gemm_bf16(b"X", 8, 8, 8, 1.0, p, 8, p, 8, 0.0, p, 8, 1, None) == -1
