@@ -66,6 +66,11 @@ struct Ooc {
   char *qr, *svd;
   double* gemm;
   size_t gemm_bytes;
+  double* gemm2;  // dgemm scratch of the SVD on the side stream
+  size_t gemm2_bytes;
+  SideStream* side = nullptr;
+  bool fold_pending = false;  // SVD of block (fold_k, fold_bi) launched, folds not yet applied
+  int64_t fold_k = 0, fold_bi = 0;
   double* buf[kBufs];
   int64_t cap;  // elements per buffer
   unsigned* status;
@@ -88,6 +93,7 @@ size_t fixed_bytes(int64_t m, int64_t n, int64_t b) {
   add(householder_scratch_bytes(b));
   add(small_svd_scratch_bytes((int)b));
   add(dgemm_scratch_bytes(std::max(m, n), b));
+  add(dgemm_scratch_bytes(b, b));
   return s + 4096;
 }
 
@@ -176,73 +182,18 @@ int right_apply(Ooc& o, int mat, double* X, int64_t ldx, int64_t rows, int64_t r
                        });
 }
 
-int ooc_step(Ooc& o, int step, int64_t k, int64_t bi) {
-  const int64_t m = o.m, n = o.n, lda = o.lda, rm = m - k, rn = n - k;
+// Waits for the side stream's SVD of block (fold_k, fold_bi) and applies its
+// folds on the compute stream: T(0:k, blk) Vs, Us^T T(blk, k+bi:), V(:, blk)
+// Vs, U(:, blk) Us and T(blk, blk) = diag(D).  Of all later passes only the
+// products from the right of T read what these write (rows blk of T), so
+// the next step calls this before its first such pass; its sketch passes and
+// QR run beside the SVD.
+int flush_folds(Ooc& o) {
+  if (!o.fold_pending) return 0;
+  o.fold_pending = false;
+  RUTV_CK(cudaStreamWaitEvent(o.cs, o.side->svd, 0));
+  const int64_t m = o.m, n = o.n, lda = o.lda, k = o.fold_k, bi = o.fold_bi, rn = n - k;
   double* T22 = o.T + k + k * lda;
-  // ---- right transform
-  if (rn > bi) {
-    RUTV_TRY(launch_philox_normal(o.seed, (uint32_t)step, 0u, 0u, rm, bi, o.G, rm, o.cs));
-    const int64_t cw = panel_len(o, rm, rn);
-    // Y = T22^T G
-    RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, rn, false, cw, false,
-                           [&](double* P, int64_t ldp, int64_t, int64_t c0, int64_t, int64_t pc) {
-                             return gemm(o, true, false, pc, bi, rm, 1.0, P, ldp, o.G, rm, 0.0,
-                                         o.Y + c0, rn);
-                           }));
-    for (int it = 0; it < o.q; ++it) {
-      // Z = T22 Y, summed over the column panels in order
-      RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, rn, false, cw, false,
-                             [&](double* P, int64_t ldp, int64_t, int64_t c0, int64_t, int64_t pc) {
-                               return gemm(o, false, false, rm, bi, pc, 1.0, P, ldp, o.Y + c0, rn,
-                                           c0 == 0 ? 0.0 : 1.0, o.Z, rm);
-                             }));
-      RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, rn, false, cw, false,
-                             [&](double* P, int64_t ldp, int64_t, int64_t c0, int64_t, int64_t pc) {
-                               return gemm(o, true, false, pc, bi, rm, 1.0, P, ldp, o.Z, rm, 0.0,
-                                           o.Y + c0, rn);
-                             }));
-    }
-    RUTV_TRY(launch_householder_qr(rn, bi, o.Y, rn, o.W, o.tau, o.qr, o.status + 2, o.status,
-                                   o.cs));
-    RUTV_TRY(wy_ws(o, rn, bi));
-    RUTV_TRY(right_apply(o, MAT_T, o.T + k * lda, lda, m, rn, bi));
-    if (o.V) RUTV_TRY(right_apply(o, MAT_V, o.V + k * n, n, n, rn, bi));
-  }
-  // ---- left transform (the panel QR also leaves the diagonal block in blk)
-  if (rm > bi) {
-    RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, bi, false, bi, true,
-                           [&](double* P, int64_t ldp, int64_t, int64_t, int64_t, int64_t) {
-                             RUTV_TRY(launch_householder_qr(rm, bi, P, ldp, o.W, o.tau, o.qr,
-                                                            o.status + 2, o.status, o.cs));
-                             RUTV_CK(cudaMemcpy2DAsync(o.blk, (size_t)bi * 8, P, (size_t)ldp * 8,
-                                                       (size_t)bi * 8, (size_t)bi,
-                                                       cudaMemcpyDeviceToDevice, o.cs));
-                             return 0;
-                           }));
-    RUTV_TRY(wy_ws(o, rm, bi));
-    if (rn > bi) {
-      const int64_t nc = rn - bi;
-      RUTV_TRY(stream_panels(o, MAT_T, T22 + bi * lda, lda, rm, nc, false, panel_len(o, rm, nc), true,
-                             [&](double* P, int64_t ldp, int64_t, int64_t, int64_t, int64_t pc) {
-                               RUTV_TRY(gemm(o, true, false, pc, bi, rm, 1.0, P, ldp, o.W, rm, 0.0,
-                                             o.X, pc));
-                               return gemm(o, false, true, rm, pc, bi, -1.0, o.WS, rm, o.X, pc, 1.0,
-                                           P, ldp);
-                             }));
-    }
-    if (o.U) RUTV_TRY(right_apply(o, MAT_U, o.U + k * m, m, m, rm, bi));
-  } else {
-    RUTV_TRY(stream_panels(o, MAT_T, T22, lda, bi, bi, false, bi, false,
-                           [&](double* P, int64_t ldp, int64_t, int64_t, int64_t, int64_t) {
-                             RUTV_CK(cudaMemcpy2DAsync(o.blk, (size_t)bi * 8, P, (size_t)ldp * 8,
-                                                       (size_t)bi * 8, (size_t)bi,
-                                                       cudaMemcpyDeviceToDevice, o.cs));
-                             return 0;
-                           }));
-  }
-  // ---- small SVD of the diagonal block and the folds
-  RUTV_TRY(launch_small_svd((int)bi, o.blk, bi, o.D, o.Us, o.Vs, o.status + 8, o.svd, o.gemm,
-                            o.gemm_bytes, o.cs));
   // strips of bi columns (T(0:k, blk), V(:, blk), U(:, blk)): P <- P F, as
   // one panel of whole columns (rows x bi fits a buffer)
   auto fold_cols = [&](int mat, double* X, int64_t ldx, int64_t rows, const double* F) {
@@ -279,6 +230,87 @@ int ooc_step(Ooc& o, int step, int64_t k, int64_t bi) {
                            RUTV_CK(cudaGetLastError());
                            return 0;
                          }));
+  return 0;
+}
+
+int ooc_step(Ooc& o, int step, int64_t k, int64_t bi) {
+  const int64_t m = o.m, n = o.n, lda = o.lda, rm = m - k, rn = n - k;
+  double* T22 = o.T + k + k * lda;
+  // ---- right transform
+  if (rn > bi) {
+    RUTV_TRY(launch_philox_normal(o.seed, (uint32_t)step, 0u, 0u, rm, bi, o.G, rm, o.cs));
+    const int64_t cw = panel_len(o, rm, rn);
+    // Y = T22^T G
+    RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, rn, false, cw, false,
+                           [&](double* P, int64_t ldp, int64_t, int64_t c0, int64_t, int64_t pc) {
+                             return gemm(o, true, false, pc, bi, rm, 1.0, P, ldp, o.G, rm, 0.0,
+                                         o.Y + c0, rn);
+                           }));
+    for (int it = 0; it < o.q; ++it) {
+      // Z = T22 Y, summed over the column panels in order
+      RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, rn, false, cw, false,
+                             [&](double* P, int64_t ldp, int64_t, int64_t c0, int64_t, int64_t pc) {
+                               return gemm(o, false, false, rm, bi, pc, 1.0, P, ldp, o.Y + c0, rn,
+                                           c0 == 0 ? 0.0 : 1.0, o.Z, rm);
+                             }));
+      RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, rn, false, cw, false,
+                             [&](double* P, int64_t ldp, int64_t, int64_t c0, int64_t, int64_t pc) {
+                               return gemm(o, true, false, pc, bi, rm, 1.0, P, ldp, o.Z, rm, 0.0,
+                                           o.Y + c0, rn);
+                             }));
+    }
+    // the previous block's SVD may still hold SMs: leave them to it
+    RUTV_TRY(launch_householder_qr(rn, bi, o.Y, rn, o.W, o.tau, o.qr, o.status + 2, o.status,
+                                   o.cs, o.fold_pending ? kSvdSms : 0));
+    RUTV_TRY(wy_ws(o, rn, bi));
+    RUTV_TRY(flush_folds(o));
+    RUTV_TRY(right_apply(o, MAT_T, o.T + k * lda, lda, m, rn, bi));
+    if (o.V) RUTV_TRY(right_apply(o, MAT_V, o.V + k * n, n, n, rn, bi));
+  }
+  // ---- left transform (the panel QR also leaves the diagonal block in blk)
+  RUTV_TRY(flush_folds(o));
+  if (rm > bi) {
+    RUTV_TRY(stream_panels(o, MAT_T, T22, lda, rm, bi, false, bi, true,
+                           [&](double* P, int64_t ldp, int64_t, int64_t, int64_t, int64_t) {
+                             RUTV_TRY(launch_householder_qr(rm, bi, P, ldp, o.W, o.tau, o.qr,
+                                                            o.status + 2, o.status, o.cs));
+                             RUTV_CK(cudaMemcpy2DAsync(o.blk, (size_t)bi * 8, P, (size_t)ldp * 8,
+                                                       (size_t)bi * 8, (size_t)bi,
+                                                       cudaMemcpyDeviceToDevice, o.cs));
+                             return 0;
+                           }));
+    RUTV_TRY(wy_ws(o, rm, bi));
+    if (rn > bi) {
+      const int64_t nc = rn - bi;
+      RUTV_TRY(stream_panels(o, MAT_T, T22 + bi * lda, lda, rm, nc, false, panel_len(o, rm, nc), true,
+                             [&](double* P, int64_t ldp, int64_t, int64_t, int64_t, int64_t pc) {
+                               RUTV_TRY(gemm(o, true, false, pc, bi, rm, 1.0, P, ldp, o.W, rm, 0.0,
+                                             o.X, pc));
+                               return gemm(o, false, true, rm, pc, bi, -1.0, o.WS, rm, o.X, pc, 1.0,
+                                           P, ldp);
+                             }));
+    }
+    if (o.U) RUTV_TRY(right_apply(o, MAT_U, o.U + k * m, m, m, rm, bi));
+  } else {
+    RUTV_TRY(stream_panels(o, MAT_T, T22, lda, bi, bi, false, bi, false,
+                           [&](double* P, int64_t ldp, int64_t, int64_t, int64_t, int64_t) {
+                             RUTV_CK(cudaMemcpy2DAsync(o.blk, (size_t)bi * 8, P, (size_t)ldp * 8,
+                                                       (size_t)bi * 8, (size_t)bi,
+                                                       cudaMemcpyDeviceToDevice, o.cs));
+                             return 0;
+                           }));
+  }
+  // ---- small SVD of the diagonal block, on the side stream: it runs beside
+  // the next step's sketch passes and QR; its folds wait for flush_folds
+  RUTV_TRY(flush_folds(o));
+  RUTV_CK(cudaEventRecord(o.side->panel, o.cs));
+  RUTV_CK(cudaStreamWaitEvent(o.side->st, o.side->panel, 0));
+  RUTV_TRY(launch_small_svd((int)bi, o.blk, bi, o.D, o.Us, o.Vs, o.status + 8, o.svd, o.gemm2,
+                            o.gemm2_bytes, o.side->st));
+  RUTV_CK(cudaEventRecord(o.side->svd, o.side->st));
+  o.fold_pending = true;
+  o.fold_k = k;
+  o.fold_bi = bi;
   return 0;
 }
 
@@ -365,7 +397,10 @@ int randutv_factor_ooc(int64_t m, int64_t n, double* A, int64_t lda, int b, int 
   o.svd = (char*)ar.take(small_svd_scratch_bytes((int)bb));
   o.gemm_bytes = dgemm_scratch_bytes(std::max(m, n), bb);
   o.gemm = (double*)ar.take(o.gemm_bytes);
+  o.gemm2_bytes = dgemm_scratch_bytes(bb, bb);
+  o.gemm2 = (double*)ar.take(o.gemm2_bytes);
   for (int i = 0; i < kBufs; ++i) o.buf[i] = (double*)ar.take((size_t)cap * 8);
+  RUTV_TRY(side_stream(&o.side));
   o.cap = cap;
   RUTV_TRY(status_words(&o.status));
   o.cs = (cudaStream_t)stream;
@@ -413,6 +448,7 @@ int randutv_factor_ooc(int64_t m, int64_t n, double* A, int64_t lda, int b, int 
     const int64_t bi = (bb < p - k) ? bb : p - k;
     RUTV_TRY(ooc_step(o, step, k, bi));
   }
+  RUTV_TRY(flush_folds(o));
   // the caller's stream, and this call's return, follow the last write-back
   RUTV_CK(cudaEventRecord(o.join, o.d2h));
   RUTV_CK(cudaStreamWaitEvent(o.cs, o.join, 0));
