@@ -106,7 +106,9 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # the raw samples go to BENCH_CLOCKS_DIR (default: bench_out/ beside this file)
+        out_dir = os.environ.get("BENCH_CLOCKS_DIR") or os.path.join(ROOT, "bench_out")
+        self.path = os.path.join(out_dir, f"clocks_rank{index}.csv")
 
     def start(self):
         try:
