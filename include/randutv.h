@@ -145,6 +145,25 @@ int randutv_factor_batched(int batch, const int64_t* m, const int64_t* n, const 
  * and CTAs per SM for the persistent grid (0 = occupancy limit). */
 int randutv_batched_set_tuning(const int* b_for_class, int nclasses, int ctas_per_sm);
 
+/* ------------------------------------------------------------------ HQRRP --
+ * Column-pivoted QR A P = Q R by HQRRP (§2.1-2.2): blocks of b pivots, each
+ * chosen by b steps of column-pivoted QR of the sketch Y = G R(k:, k:), G of
+ * size b x (m - k) with i.i.d. N(0,1) entries, drawn anew at every step, and
+ * followed by an unpivoted Householder QR of the chosen columns.  FP64;
+ * asynchronous on `stream` (arg 10); all pointers DEVICE.
+ *   m, n (1, 2)  m >= n >= 1.
+ *   A (3)        m x n with lda (4) >= m, read only (R may be A when lda == m).
+ *   b (5)        1 <= b <= 256.
+ *   seed (6)     G of step i is the transpose of the m-k x b array that
+ *                randutv_philox_normal(seed, i, 0, 6, ...) gives.
+ *   Q (7)        m x m (ld m), or NULL.
+ *   R (8)        m x n (ld m): R, upper trapezoidal with exact zeros.
+ *   perm (9)     n int64: column j of A P is column perm[j] of A.
+ * Ties between pivot candidates go to the lowest column position.  Device
+ * errors are read with randutv_stream_status(). */
+int randutv_hqrrp(int64_t m, int64_t n, const double* A, int64_t lda, int b, uint64_t seed,
+                  double* Q, double* R, int64_t* perm, void* stream);
+
 /* ------------------------------------------------------------- out of HBM --
  * The factorization of a matrix that stays in HOST memory (§3.2: the
  * out-of-core setting, here the device's HBM against the host's memory).

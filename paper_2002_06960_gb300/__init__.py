@@ -13,7 +13,7 @@ _BINDING_NAMES = (
     "randutv_wy_factor", "randutv_small_svd", "randutv_dgemm", "randutv_workspace_bytes",
     "randutv_finalize", "randutv_launch_count", "colmajor_empty", "to_colmajor", "lib",
     "RandutvError", "exported_names", "randutv_profile_enable", "randutv_profile_read", "randutv_factor_mixed",
-    "randutv_gemm_bf16", "randutv_factor_ooc", "randutv_ooc_min_device_bytes",
+    "randutv_gemm_bf16", "randutv_factor_ooc", "randutv_ooc_min_device_bytes", "randutv_hqrrp",
 )
 
 

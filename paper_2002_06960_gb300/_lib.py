@@ -56,6 +56,7 @@ _SIGS = {
     "randutv_factor_batched": (c_int, [c_int, c_vp, c_vp, c_vp, c_vp, c_int, c_int, c_u64, c_vp,
                                        c_vp, c_vp, c_vp, c_vp]),
     "randutv_batched_set_tuning": (c_int, [c_vp, c_int, c_int]),
+    "randutv_hqrrp": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_u64, c_vp, c_vp, c_vp, c_vp]),
     "randutv_ooc_min_device_bytes": (ctypes.c_size_t, [c_i64, c_i64, c_int]),
     "randutv_factor_ooc": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_u64, c_vp, c_vp,
                                    ctypes.c_size_t, c_vp, c_vp]),
@@ -199,6 +200,19 @@ def randutv_factor_host(A_host, b, q, seed, U_host=None, T_host=None, V_host=Non
     _check("randutv_factor_host", lib().randutv_factor_host(
         m, n, _ptr(A_host), lda, b, q, seed, _ptr(U_host), _ptr(T_host), _ptr(V_host)))
     return U_host, T_host, V_host
+
+
+def randutv_hqrrp(A, b, seed, want_q=True):
+    """A P = Q R by HQRRP on a column-major float64 CUDA tensor (m >= n).
+    Returns (Q or None, R, perm) with perm an int64 CUDA tensor."""
+    m, n = A.shape
+    lda = _colmajor(_dev(A, "A"), m, n, "A")
+    R = colmajor_empty(m, n, device=A.device)
+    Q = colmajor_empty(m, m, device=A.device) if want_q else None
+    perm = torch.empty(n, dtype=torch.int64, device=A.device)
+    _check("randutv_hqrrp", lib().randutv_hqrrp(m, n, _ptr(A), lda, b, seed, _ptr(Q), _ptr(R),
+                                                 _ptr(perm), _stream()))
+    return Q, R, perm
 
 
 def randutv_ooc_min_device_bytes(m, n, b):

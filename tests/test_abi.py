@@ -104,6 +104,12 @@ def test_argument_errors_return_before_any_device_work(libpath):
     assert L.randutv_factor_ooc(64, 40, p, 64, 300, 1, 0, None, None, need, None, None) == -5
     assert L.randutv_factor_ooc(64, 40, p, 64, 8, 17, 0, None, None, need, None, None) == -6
     assert L.randutv_factor_ooc(64, 40, p, 64, 8, 1, 0, None, None, need - 1, None, None) == -10
+    # randutv_hqrrp: m >= n, 1 <= b <= 256, R and perm given
+    assert L.randutv_hqrrp(40, 64, p, 40, 8, 0, None, p, p, None) == -2
+    assert L.randutv_hqrrp(64, 40, p, 32, 8, 0, None, p, p, None) == -4
+    assert L.randutv_hqrrp(64, 40, p, 64, 0, 0, None, p, p, None) == -5
+    assert L.randutv_hqrrp(64, 40, p, 64, 8, 0, None, None, p, None) == -8
+    assert L.randutv_hqrrp(64, 40, p, 64, 8, 0, None, p, None, None) == -9
     # randutv_gemm_bf16: planes must be 1 or 3
     assert L.randutv_gemm_bf16(b"N", 8, 8, 8, 1.0, p, 8, p, 8, 0.0, p, 8, 2, None) == -13
     assert L.randutv_gemm_bf16(b"X", 8, 8, 8, 1.0, p, 8, p, 8, 0.0, p, 8, 1, None) == -1
