@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true",
                     help="skip the batched line (4096 matrices of sizes in [64, 1024])")
     ap.add_argument("--batched-count", type=int, default=4096)
+    ap.add_argument("--no-hqrrp", action="store_true",
+                    help="skip the column-pivoted QR (HQRRP) line")
     ap.add_argument("--no-ooc", action="store_true",
                     help="skip the out-of-HBM form (T, U, V in host memory)")
     ap.add_argument("--no-backward", action="store_true",
@@ -344,6 +346,58 @@ def run_ooc(args, A_host, fp64_ms=None, device_gib=1.0):
     if fp64_ms:
         out["time_vs_in_hbm"] = round(secs / (fp64_ms * 1e-3), 3)
     return out
+
+
+# ----------------------------------------------------------------- HQRRP
+
+def hqrrp_flops(m, n, b):
+    """Leading-order flops of HQRRP with Q, summed per block step: the sketch
+    2 bi rm rn, the panel QR 2 bi^2 (rm - bi/3) plus rm bi^2 for W S, the
+    left update 4 rm (rn - bi) bi and the update of Q 4 m rm bi (the column-
+    pivoted QR of the bi x rn sketch, O(bi^2 rn), is not counted)."""
+    t, k = 0.0, 0
+    while k < n:
+        bi = min(b, n - k)
+        rm, rn = m - k, n - k
+        t += (2 * bi * rm * rn + 2 * bi * bi * (rm - bi / 3) + rm * bi * bi
+              + 4 * rm * (rn - bi) * bi + 4 * m * rm * bi)
+        k += bi
+    return t
+
+
+def run_hqrrp(args, steps=1, warmup=1):
+    """HQRRP (§2.2): A P = Q R at the headline size, FP64 on the device."""
+    import paper_2002_06960_gb300 as pkg
+
+    n, b = args.n, args.b
+    g = torch.Generator(device="cuda")
+    g.manual_seed(args.seed)
+    A = pkg.colmajor_empty(n, n)
+    A.copy_(torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64))
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for _ in range(warmup):
+            pkg.randutv_hqrrp(A, b, 0, True)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            Q, R, perm = pkg.randutv_hqrrp(A, b, 0, True)
+        e1.record(stream)
+        st = pkg.randutv_stream_status()
+    e1.synchronize()
+    if st != 0:
+        raise RuntimeError(f"HQRRP failed with status {st}")
+    ms = e0.elapsed_time(e1) / steps
+    rows = torch.randperm(n, generator=torch.Generator().manual_seed(0))[:64].cuda()
+    recon = float(torch.linalg.norm(Q[rows] @ R - A[rows][:, perm]) / torch.linalg.norm(A[rows]))
+    flops = hqrrp_flops(n, n, b)
+    peak, _, _ = fp64_peak()
+    return {"workload": f"hqrrp_fp64_n{n}_b{b}", "value": round(flops / (ms * 1e-3) / 1e12, 4),
+            "unit": "TFLOP/s", "ms_per_step": round(ms, 1), "steps": steps, "warmup": warmup,
+            "dtype": "f64", "input": "i.i.d. N(0,1), seeded", "outputs": "Q, R, P",
+            "algorithmic_flops": flops, "fp64_roofline_frac": round(flops / (ms * 1e-3) / 1e12 / peak, 4),
+            "errors": {"recon_sampled_rows": recon}}
 
 
 # ------------------------------------------------------- mixed precision
@@ -686,6 +740,11 @@ def main():
             print(json.dumps(out), flush=True)
         return
     out, A_host = run_ours(args, world, rank, local)
+    if world == 1 and not args.no_hqrrp:
+        try:
+            out["hqrrp"] = run_hqrrp(args)
+        except Exception as e:  # report, never hide
+            out["hqrrp"] = {"error": repr(e)}
     if world == 1 and not args.no_ooc:
         try:
             out["out_of_hbm"] = run_ooc(args, A_host, fp64_ms=out["ms_per_step"])
