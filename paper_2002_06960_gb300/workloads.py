@@ -3,6 +3,7 @@
     python -m paper_2002_06960_gb300.workloads fp64 --n 4096 --b 128 --q 1
     python -m paper_2002_06960_gb300.workloads mixed --n 4096 --b 256 --q 2 --steps 1
     python -m paper_2002_06960_gb300.workloads batched --count 152 --b 32
+    python -m paper_2002_06960_gb300.workloads hqrrp --n 4096 --b 128
 
 Each builds a seeded input, runs the factorization through the public API,
 waits for it, and exits non-zero if the library reports an error.
@@ -61,9 +62,21 @@ def _batched(args):
     return bad
 
 
+def _hqrrp(args):
+    import paper_2002_06960_gb300 as pkg
+    n = args.n
+    g = torch.Generator(device="cuda")
+    g.manual_seed(args.seed)
+    A = pkg.colmajor_empty(n, n)
+    A.copy_(torch.randn(n, n, generator=g, device="cuda", dtype=torch.float64))
+    for _ in range(args.reps):
+        pkg.randutv_hqrrp(A, args.b, 0, True)
+    return pkg.randutv_stream_status()
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.splitlines()[0])
-    ap.add_argument("kind", choices=["fp64", "mixed", "batched"])
+    ap.add_argument("kind", choices=["fp64", "mixed", "batched", "hqrrp"])
     ap.add_argument("--n", type=int, default=4096)
     ap.add_argument("--b", type=int, default=0, help="block size (default: 128 FP64, 256 mixed, 32 batched)")
     ap.add_argument("--q", type=int, default=-1, help="power steps (default: 1 FP64 and batched, 2 mixed)")
@@ -72,12 +85,12 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=1)
     args = ap.parse_args(argv)
-    defaults = {"fp64": (128, 1), "mixed": (256, 2), "batched": (32, 1)}[args.kind]
+    defaults = {"fp64": (128, 1), "mixed": (256, 2), "batched": (32, 1), "hqrrp": (128, 0)}[args.kind]
     if args.b <= 0:
         args.b = defaults[0]
     if args.q < 0:
         args.q = defaults[1]
-    st = {"fp64": _fp64, "mixed": _mixed, "batched": _batched}[args.kind](args)
+    st = {"fp64": _fp64, "mixed": _mixed, "batched": _batched, "hqrrp": _hqrrp}[args.kind](args)
     print(f"{args.kind}: status {st}")
     return 0 if st == 0 else 1
 
