@@ -7,7 +7,9 @@
  * orthogonal and T (m x n) upper triangular, one block of b columns per step:
  * a Gaussian sketch and power iteration give the block of V, a Householder QR
  * of the new column panel gives the block of U, and a b x b SVD makes the
- * diagonal block of T diagonal.
+ * diagonal block of T diagonal.  The same library holds the paper's other
+ * factorization, HQRRP (§2: column-pivoted QR A P = Q R with pivots chosen on
+ * a sketch), and the factorization of a matrix kept in host memory (§3.2).
  *
  * Conventions for every entry point below:
  *  - Matrices are column-major with a leading dimension (ld >= rows).
@@ -15,8 +17,9 @@
  *    the name ends in _host.  The caller owns every buffer it passes; the
  *    library never frees caller memory.
  *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
- *    stream).  Entry points ending in _ex are asynchronous on that stream;
- *    the others synchronize before returning.
+ *    stream).  Each entry point states whether it is asynchronous on its
+ *    stream (device errors then come from randutv_stream_status) or
+ *    synchronizes before returning.
  *  - Return value: 0 on success; -i if argument i (1-based) is invalid
  *    (LAPACK style); a positive randutv_status otherwise.  No C++ exception
  *    crosses this boundary.
@@ -219,6 +222,8 @@ int randutv_gemm_bf16(char transa, int64_t M, int64_t N, int64_t K, float alpha,
 
 /* ------------------------------------------------------------ components --
  * The steps of one block, exposed so that each can be checked on its own.
+ * All are asynchronous on `stream` (the last argument); device errors (a
+ * bounded wait that ran out) are read with randutv_stream_status().
  */
 
 /* Gaussian sketch of one step (§3.1, construction of V-hat, step 1): G is
