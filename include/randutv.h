@@ -314,6 +314,13 @@ const char* randutv_last_error(void);
 /* Number of kernel launches issued by this process since the last reset. */
 uint64_t randutv_launch_count(int reset);
 
+/* Failure-detection self-test: launches one CTA at a grid barrier sized for
+ * two CTAs on `stream`, so that the count it waits on never completes.  The
+ * wait is bounded (about two seconds), after which the kernel records
+ * RANDUTV_ETIMEOUT and returns, leaving the context usable.  Returns
+ * RANDUTV_ETIMEOUT when that happened as designed, -100 otherwise. */
+int randutv_selftest_wait_timeout(void* stream);
+
 /* Tracing.  While enabled (on != 0), every kernel launch of the library is
  * bracketed by a pair of CUDA events on its stream and tagged with its kernel
  * class and the algorithmic flops and bytes of that launch.  Enabling clears

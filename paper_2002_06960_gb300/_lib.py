@@ -44,6 +44,7 @@ _SIGS = {
     "randutv_strerror": (ctypes.c_char_p, [c_int]),
     "randutv_last_error": (ctypes.c_char_p, []),
     "randutv_launch_count": (c_u64, [c_int]),
+    "randutv_selftest_wait_timeout": (c_int, [c_vp]),
     "randutv_factor_mixed": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_u64, c_vp, c_vp,
                                      c_vp, c_int, c_vp]),
     "randutv_gemm_bf16": (c_int, [ctypes.c_char, c_i64, c_i64, c_i64, ctypes.c_float, c_vp, c_i64,

@@ -216,6 +216,12 @@ __global__ void set_diag_block_kernel(int64_t bi, const double* D, double* T, in
   }
 }
 
+// One CTA at a barrier for two CTAs (the failure-detection self-test).
+__global__ void lone_barrier_kernel(unsigned* bar, unsigned* err) {
+  unsigned epoch = 0;
+  grid_barrier(bar, 2u, err, 901u, epoch);
+}
+
 int grid_for(int64_t total, int threads = 256) {
   int64_t blocks = (total + threads - 1) / threads;
   const int64_t cap = (int64_t)dev_info().sms * 8;
@@ -540,6 +546,23 @@ const char* randutv_profile_class_name(int cls) {
                                         "wy_factor", "jacobi_svd", "other", "bgemm_tcgen05",
                                         "convert", "jacobi_svd_fp32"};
   return (cls >= 0 && cls < K_NCLASS) ? names[cls] : "?";
+}
+
+// Failure detection self-test: one CTA arrives at a grid barrier sized for
+// two, so the counter it waits on never completes; the bounded wait gives
+// up after kWaitLimitNs and records RANDUTV_ETIMEOUT with site 901.
+int randutv_selftest_wait_timeout(void* stream) {
+  cudaStream_t st = (cudaStream_t)stream;
+  unsigned* status = nullptr;
+  RUTV_TRY(status_words(&status));
+  RUTV_CK(cudaMemsetAsync(status, 0, 64 * sizeof(unsigned), st));
+  lone_barrier_kernel<<<1, 32, 0, st>>>(status + 2, status);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  RUTV_CK(cudaStreamSynchronize(st));
+  unsigned h[2] = {0, 0};
+  RUTV_CK(cudaMemcpy(h, status, sizeof h, cudaMemcpyDeviceToHost));
+  return (h[0] == (unsigned)RANDUTV_ETIMEOUT && h[1] == 901u) ? (int)h[0] : -100;
 }
 
 uint64_t randutv_launch_count(int reset) {
