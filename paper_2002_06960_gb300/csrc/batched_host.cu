@@ -73,12 +73,14 @@ extern "C" {
 int randutv_batched_set_tuning(const int* b_for_class, int nclasses, int ctas_per_sm) {
   if (nclasses < 0 || nclasses > kClasses) return -2;
   if (ctas_per_sm < 0 || ctas_per_sm > 16) return -3;
-  std::lock_guard<std::mutex> lk(g_tune_mu);
-  for (int c = 0; c < kClasses; ++c) {
-    int b = (b_for_class && c < nclasses) ? b_for_class[c] : 0;
+  int table[kClasses];
+  for (int c = 0; c < kClasses; ++c) {  // validate all first: an error changes nothing
+    const int b = (b_for_class && c < nclasses) ? b_for_class[c] : 0;
     if (b != 0 && b != 16 && b != 32 && b != 64) return -1;
-    g_b_table[c] = b;
+    table[c] = b;
   }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  for (int c = 0; c < kClasses; ++c) g_b_table[c] = table[c];
   g_ctas_per_sm = ctas_per_sm;
   return 0;
 }
