@@ -25,6 +25,12 @@
  *    crosses this boundary.
  *  - Scratch memory is allocated by the library on first use per device and
  *    kept until randutv_finalize(); it grows when a larger problem needs it.
+ *    All entry points on one device share that scratch (and the library's
+ *    side and copy streams), so calls whose device work may overlap, such as
+ *    asynchronous calls on different streams or calls from several host
+ *    threads, must be serialized by the caller: issue them on one stream,
+ *    or wait for one before starting the next.  A batched plan owns its own
+ *    workspace.
  *  - Device-side waits are bounded (about two seconds); a wait that runs out
  *    makes the call return RANDUTV_ETIMEOUT and leaves the outputs undefined.
  */
