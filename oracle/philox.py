@@ -23,6 +23,13 @@ the same G without passing it around:
   j2 = (x2 >> 5) * 2^26 + (x3 >> 6),  u2 = j2 * 2^-53        in [0, 1)
 * Box-Muller (Box & Muller 1958): rho = sqrt(-2 ln u1),
   G[2p] = rho cos(2 pi u2), G[2p+1] = rho sin(2 pi u2).
+
+The batched form of the library (many small FP32 factorizations in one
+launch) draws its sketch from the same words with 24-bit uniforms,
+u1 = ((x0 >> 8) + 1) 2^-24 in (0, 1] and u2 = (x2 >> 8) 2^-24 in [0, 1)
+(x1 and x3 unused), counter (p, step, matrix index, 0), and FP32 normals.
+``box_muller_f32`` is that transform: the exact Box-Muller value of the two
+FP32 uniforms, evaluated in FP64 and rounded once to FP32.
 """
 from __future__ import annotations
 
@@ -73,21 +80,57 @@ def uniforms(words: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
     return u1, u2
 
 
-def normal_pairs(seed: int, step: int, matrix_id: int, stream: int,
-                 npairs: int) -> np.ndarray:
-    """Standard normals 2p, 2p+1 for pairs p = 0 .. npairs-1, as a flat array."""
+def box_muller(words: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """The pair of normals (even element, odd element) of each word quadruple (..., 4)."""
+    u1, u2 = uniforms(words)
+    rho = np.sqrt(-2.0 * np.log(u1))
+    return rho * np.cos(2.0 * np.pi * u2), rho * np.sin(2.0 * np.pi * u2)
+
+
+def uniforms_f32(words: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """(u1, u2) of the batched form: 24 bits each from x0 and x2, exact in FP32."""
+    w = words.astype(np.uint64)
+    u1 = ((w[..., 0] >> np.uint64(8)) + np.uint64(1)).astype(np.float64) * 2.0 ** -24
+    u2 = (w[..., 2] >> np.uint64(8)).astype(np.float64) * 2.0 ** -24
+    return u1, u2
+
+
+def box_muller_f32(words: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """The batched form's FP32 pair of normals: Box-Muller of the 24-bit uniforms in FP64,
+    rounded once to FP32."""
+    u1, u2 = uniforms_f32(words)
+    rho = np.sqrt(-2.0 * np.log(u1))
+    return ((rho * np.cos(2.0 * np.pi * u2)).astype(np.float32),
+            (rho * np.sin(2.0 * np.pi * u2)).astype(np.float32))
+
+
+def _words(seed: int, step: int, matrix_id: int, stream: int, npairs: int) -> np.ndarray:
     p = np.arange(npairs, dtype=np.uint64)
     ctr = np.empty((npairs, 4), dtype=np.uint64)
     ctr[:, 0] = p & MASK32
     ctr[:, 1] = np.uint64(step) & MASK32
     ctr[:, 2] = np.uint64(matrix_id) & MASK32
     ctr[:, 3] = np.uint64(stream) & MASK32
-    words = philox4x32_10(ctr, seed_key(seed))
-    u1, u2 = uniforms(words)
-    rho = np.sqrt(-2.0 * np.log(u1))
+    return philox4x32_10(ctr, seed_key(seed))
+
+
+def normal_pairs(seed: int, step: int, matrix_id: int, stream: int,
+                 npairs: int) -> np.ndarray:
+    """Standard normals 2p, 2p+1 for pairs p = 0 .. npairs-1, as a flat array."""
+    even, odd = box_muller(_words(seed, step, matrix_id, stream, npairs))
     out = np.empty(2 * npairs, dtype=np.float64)
-    out[0::2] = rho * np.cos(2.0 * np.pi * u2)
-    out[1::2] = rho * np.sin(2.0 * np.pi * u2)
+    out[0::2] = even
+    out[1::2] = odd
+    return out
+
+
+def normal_pairs_f32(seed: int, step: int, matrix_id: int, stream: int,
+                     npairs: int) -> np.ndarray:
+    """The batched form's FP32 normals 2p, 2p+1 for p = 0 .. npairs-1, as a flat array."""
+    even, odd = box_muller_f32(_words(seed, step, matrix_id, stream, npairs))
+    out = np.empty(2 * npairs, dtype=np.float32)
+    out[0::2] = even
+    out[1::2] = odd
     return out
 
 
@@ -96,4 +139,12 @@ def sketch(seed: int, step: int, rows: int, cols: int, matrix_id: int = 0,
     """The rows x cols Gaussian sketch of one step, column-major element order."""
     count = rows * cols
     flat = normal_pairs(seed, step, matrix_id, stream, (count + 1) // 2)[:count]
+    return flat.reshape(cols, rows).T.copy()
+
+
+def sketch_f32(seed: int, step: int, rows: int, cols: int, matrix_id: int = 0,
+               stream: int = STREAM_SKETCH) -> np.ndarray:
+    """The batched form's FP32 sketch of one step (same element order as ``sketch``)."""
+    count = rows * cols
+    flat = normal_pairs_f32(seed, step, matrix_id, stream, (count + 1) // 2)[:count]
     return flat.reshape(cols, rows).T.copy()

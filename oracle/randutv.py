@@ -159,8 +159,13 @@ def block_schedule(m: int, n: int, b: int):
     return out
 
 
-def sketch(seed: int, step: int, rows: int, cols: int, matrix_id: int = 0) -> torch.Tensor:
-    """G of one step: i.i.d. N(0,1), rows x cols (§3.1, V-hat step 1)."""
+def sketch(seed: int, step: int, rows: int, cols: int, matrix_id: int = 0,
+           f32: bool = False) -> torch.Tensor:
+    """G of one step: i.i.d. N(0,1), rows x cols (§3.1, V-hat step 1).
+
+    ``f32`` draws the batched form's FP32 normals (returned as FP64 values)."""
+    if f32:
+        return torch.from_numpy(philox.sketch_f32(seed, step, rows, cols, matrix_id)).to(f64)
     return torch.from_numpy(philox.sketch(seed, step, rows, cols, matrix_id))
 
 
@@ -174,14 +179,16 @@ def range_basis(T22: torch.Tensor, G: torch.Tensor, q: int) -> torch.Tensor:
 
 def randutv(A: torch.Tensor, b: int, q: int, seed: int, want_u: bool = True,
             want_v: bool = True, matrix_id: int = 0, max_steps: int | None = None,
-            state: Factorization | None = None, svd: bool = True) -> Factorization:
+            state: Factorization | None = None, svd: bool = True,
+            sketch_f32: bool = False) -> Factorization:
     """A = U T V^T by blocked randUTV.
 
     ``max_steps`` stops after that many steps (a partial factorization);
     ``state`` resumes from the result of an earlier call.  ``svd=False``
     leaves out the small SVDs (T is then block upper triangular); the spans
     of U(:, 0:k) and V(:, 0:k) at every block boundary k, and the trailing
-    matrices of later steps, do not depend on them.
+    matrices of later steps, do not depend on them.  ``sketch_f32`` draws
+    every G from the batched form's FP32 generator (the arithmetic stays FP64).
     """
     A = A.to(f64)
     m, n = A.shape
@@ -207,7 +214,7 @@ def randutv(A: torch.Tensor, b: int, q: int, seed: int, want_u: bool = True,
         # (the operands are copied out before each update is written back, so
         # that the function can also be differentiated by torch autograd)
         if right:
-            G = sketch(seed, i, rm, bi, matrix_id)
+            G = sketch(seed, i, rm, bi, matrix_id, f32=sketch_f32)
             Y = range_basis(T[k:, k:].clone(), G, q)
             W, tau, _ = householder_qr(Y)
             S = wy_factor(W, tau)

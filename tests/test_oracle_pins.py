@@ -52,6 +52,71 @@ def test_uniform_extremes():
     assert u1[0] == 1.0 and u2[0] == 1.0 - 2.0 ** -53
 
 
+# Hand-worked words for the Box-Muller assignment (the reading of the sketch
+# generator: u1 from x0, x1 with the +1 offset, u2 from x2, x3; cos to the
+# even element, sin to the odd one).  Each case is worked out by hand below.
+def test_box_muller_hand_worked_words():
+    w = np.array([[1 << 31, 0, 1 << 30, 0]], dtype=np.uint32)
+    # j1 = (2^31 >> 5) 2^26 = 2^52 -> u1 = (2^52 + 1) 2^-53 = 1/2 + 2^-53
+    # j2 = (2^30 >> 5) 2^26 = 2^51 -> u2 = 1/4, angle pi/2
+    # rho = sqrt(-2 ln(1/2 + 2^-53)) = sqrt(2 ln 2) (1 - 2^-52 / (2 ln 2)) to first order
+    even, odd = philox.box_muller(w)
+    rho = math.sqrt(2.0 * math.log(2.0))
+    assert abs(odd[0] - rho) <= 4e-16 * rho          # sin(pi/2) = 1: all of rho on the odd element
+    assert abs(even[0]) < 1e-15                      # cos(pi/2) = 0
+    # swapping the roles of the two uniforms would give u1 = 1/4, u2 = 1/2:
+    # (-sqrt(2 ln 4), 0); swapping cos and sin would give (rho, 0)
+    w = np.array([[0, 0, 0, 0]], dtype=np.uint32)
+    # j1 = 0 -> u1 = 2^-53 (the +1 keeps ln finite); u2 = 0 -> (rho, 0), rho = sqrt(106 ln 2)
+    even, odd = philox.box_muller(w)
+    assert abs(even[0] - math.sqrt(106.0 * math.log(2.0))) <= 4e-16 * 8.6
+    assert odd[0] == 0.0
+    w = np.array([[0, 0xFFFFFFFF, 0, 0]], dtype=np.uint32)
+    # j1 = 0xFFFFFFFF >> 6 = 2^26 - 1 -> u1 = 2^26 2^-53 = 2^-27; rho = sqrt(54 ln 2)
+    even, odd = philox.box_muller(w)
+    assert abs(even[0] - math.sqrt(54.0 * math.log(2.0))) <= 4e-16 * 6.2
+    w = np.array([[0xFFFFFFFF, 0xFFFFFFFF, 1 << 31, 0]], dtype=np.uint32)
+    # j1 = 2^53 - 1 -> u1 = 1, rho = 0; u2 = 1/2 -> both normals are (-)0
+    even, odd = philox.box_muller(w)
+    assert even[0] == 0.0 and odd[0] == 0.0
+
+
+def test_box_muller_f32_hand_worked_words():
+    # batched form: u1 = ((x0 >> 8) + 1) 2^-24, u2 = (x2 >> 8) 2^-24, x1 and x3 unused
+    w = np.array([[0x7FFFFF00, 0xABCDEF12, 1 << 30, 0x12345678]], dtype=np.uint32)
+    # x0 >> 8 = 2^23 - 1 -> u1 = 1/2; x2 >> 8 = 2^22 -> u2 = 1/4: (0, sqrt(2 ln 2))
+    even, odd = philox.box_muller_f32(w)
+    assert even.dtype == np.float32
+    assert odd[0] == np.float32(math.sqrt(2.0 * math.log(2.0)))
+    assert abs(float(even[0])) < 1e-15
+    w = np.array([[0, 0, 0x80000000, 0]], dtype=np.uint32)
+    # u1 = 2^-24 -> rho = sqrt(48 ln 2); u2 = 1/2 -> (-rho, 0)
+    even, odd = philox.box_muller_f32(w)
+    assert even[0] == np.float32(-math.sqrt(48.0 * math.log(2.0)))
+    assert abs(float(odd[0])) < 1e-14
+    u1, u2 = philox.uniforms_f32(np.array([[0xFFFFFFFF, 0, 0xFFFFFFFF, 0]], dtype=np.uint32))
+    assert u1[0] == 1.0 and u2[0] == 1.0 - 2.0 ** -24
+
+
+def test_box_muller_f32_distribution_and_layout():
+    from scipy import stats
+    x = philox.normal_pairs_f32(seed=5, step=1, matrix_id=3, stream=0, npairs=100_000)
+    assert x.dtype == np.float32
+    xd = x.astype(np.float64)
+    n = xd.size
+    assert abs(xd.mean()) < 5.0 / math.sqrt(n)
+    assert abs(xd.var() - 1.0) < 5.0 * math.sqrt(2.0 / n)
+    assert stats.kstest(xd, "norm").pvalue > 1e-3
+    assert abs(np.corrcoef(xd[0::2], xd[1::2])[0, 1]) < 5.0 / math.sqrt(n / 2)
+    G = philox.sketch_f32(5, 1, 9, 4, matrix_id=3)
+    flat = philox.normal_pairs_f32(5, 1, 3, 0, 18)
+    assert np.array_equal(G, flat.reshape(4, 9).T)
+    # the same words as the FP64 generator: the two sketches agree to the
+    # 24-bit uniforms' resolution (the normals differ by about 2^-24 |ln u1|^-1/2)
+    G64 = philox.sketch(5, 1, 9, 4, matrix_id=3)
+    assert np.allclose(G, G64, rtol=0, atol=2e-3)
+
+
 def test_box_muller_distribution():
     from scipy import stats
     x = philox.normal_pairs(seed=11, step=3, matrix_id=0, stream=0, npairs=100_000)
