@@ -111,7 +111,12 @@ int randutv_stream_status(void* stream);
  * every compact-WY update and the fold-back take the six-product BF16 split,
  * which is FP32-accurate; the Householder vectors and norms, the WY factor S
  * and the b x b SVD are FP64.  The sketch is RNE(bf16) of the FP64 sketch
- * of randutv_philox_normal. */
+ * of randutv_philox_normal.  A run that completes every step ends with one
+ * re-orthogonalisation pass: with E = X^T X - I for X = U, V (its diagonal
+ * summed in FP64) and Phi = striu(E) + diag(E)/2, U <- U (I - Phi_U),
+ * V <- V (I - Phi_V^T) and T <- (I + Phi_U) T (I + Phi_V), which keeps
+ * U T V^T and leaves U and V orthogonal to FP32 rounding; the off-diagonal
+ * entries this leaves inside the diagonal blocks of T are zeroed. */
 int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int b, int q,
                          uint64_t seed, float* U, float* T, float* V, int max_steps,
                          void* stream);
@@ -121,9 +126,9 @@ int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int 
  * block steps of §3.1 / Fig. 2, in ONE persistent launch: each CTA takes the
  * next matrix from a device queue ordered by descending cost.  Arithmetic:
  * FP32 storage and FFMA products; Householder norms and scalars in FP64;
- * FP32 one-sided Jacobi for the b x b SVD; the sketch uses the Philox words
- * of randutv_philox_normal with counter (pair, step, matrix index, 0) and a
- * single-precision Box-Muller (u1 = ((x0 >> 8) + 1) 2^-24, u2 = (x2 >> 8) 2^-24).
+ * FP32 one-sided Jacobi for the b x b SVD; the sketch of step i of matrix j
+ * is randutv_philox_normal_f32(seed, i, j, 0, ...): the Philox words of
+ * randutv_philox_normal with a single-precision Box-Muller.
  *   batch (2)        number of matrices.
  *   m, n, lda (3,4,7) HOST arrays of length batch.
  *   A (5)            HOST array of DEVICE pointers, matrix i is m[i] x n[i].
@@ -242,6 +247,15 @@ int randutv_gemm_bf16(char transa, int64_t M, int64_t N, int64_t K, float alpha,
 int randutv_philox_normal(uint64_t seed, uint32_t step, uint32_t matrix_id, uint32_t stream_id,
                           int64_t rows, int64_t cols, double* G, void* stream);
 
+/* The batched form's FP32 sketch (the generator randutv_factor_batched draws
+ * with): the same words and element order as randutv_philox_normal, 24-bit
+ * uniforms u1 = ((x0 >> 8) + 1) 2^-24 in (0, 1] and u2 = (x2 >> 8) 2^-24 in
+ * [0, 1), and sqrt(-2 ln u1) (cos, sin)(2 pi u2) in FP32.  G is rows x cols
+ * FP32, ld = rows. */
+int randutv_philox_normal_f32(uint64_t seed, uint32_t step, uint32_t matrix_id,
+                              uint32_t stream_id, int64_t rows, int64_t cols, float* G,
+                              void* stream);
+
 /* Raw Philox4x32-10 words for counters (c0 + i, c1, c2, c3), i = 0..count-1;
  * out is 4*count uint32 (device). */
 int randutv_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
@@ -260,10 +274,11 @@ int randutv_householder_qr(int64_t r, int64_t c, double* panel, int64_t ld, doub
 
 /* randutv_householder_qr without any memory allocation (the paper has no
  * counterpart; this is a service to callers).
- * Some callers cannot allocate device memory at all: code running while a
- * CUDA graph is being captured, where cudaMalloc is not allowed; programs
- * that hand every byte of the GPU to their own allocator or memory pool; and
- * real-time loops that cannot afford an allocation's latency or failure.
+ * Some callers cannot let a library allocate device memory: programs whose
+ * own allocator or memory pool already owns all of the GPU's memory, where a
+ * cudaMalloc from the library would fail or fragment the pool; and latency-
+ * bound loops that cannot pay for cudaMalloc/cudaFree, which may block the
+ * host and synchronize the device, or handle an allocation failing midway.
  * This entry point serves them: it calls no cudaMalloc, cudaFree or other
  * allocating routine.  Its scratch is a fixed array inside the library
  * (about 388 KiB: partial sums for up to 192 SMs x 256 columns, plus its
@@ -278,8 +293,9 @@ int randutv_householder_qr(int64_t r, int64_t c, double* panel, int64_t ld, doub
  *   The first call on a device looks up the array's device address (once
  *   per device, with that device current); make that first call before any
  *   stream capture.
- *   All calls share the one array, so calls that overlap on the GPU (other
- *   streams, other host threads) race and must be serialized by the caller. */
+ *   All calls share the one array and it keeps the last call's contents, so
+ *   calls that overlap on the GPU (other streams, other host threads) race
+ *   and must be serialized by the caller. */
 int randutv_householder_qr_noalloc(int64_t r, int64_t c, double* panel, int64_t ld, double* W,
                                    double* tau, void* stream);
 
@@ -324,7 +340,9 @@ uint64_t randutv_launch_count(int reset);
  * two CTAs on `stream`, so that the count it waits on never completes.  The
  * wait is bounded (about two seconds), after which the kernel records
  * RANDUTV_ETIMEOUT and returns, leaving the context usable.  Returns
- * RANDUTV_ETIMEOUT when that happened as designed, -100 otherwise. */
+ * RANDUTV_ETIMEOUT when that happened as designed; any other device status
+ * as it is (its site in randutv_last_error); -100 when the wait completed
+ * without a timeout being recorded. */
 int randutv_selftest_wait_timeout(void* stream);
 
 /* Tracing.  While enabled (on != 0), every kernel launch of the library is

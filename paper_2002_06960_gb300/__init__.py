@@ -9,7 +9,7 @@ from . import inputs  # noqa: F401
 
 _BINDING_NAMES = (
     "randutv_factor", "randutv_factor_ex", "randutv_factor_host", "randutv_stream_status",
-    "randutv_philox_normal", "randutv_philox_words", "randutv_householder_qr",
+    "randutv_philox_normal", "randutv_philox_normal_f32", "randutv_philox_words", "randutv_householder_qr",
     "randutv_wy_factor", "randutv_small_svd", "randutv_dgemm", "randutv_workspace_bytes",
     "randutv_finalize", "randutv_launch_count", "colmajor_empty", "to_colmajor", "lib",
     "RandutvError", "exported_names", "randutv_profile_enable", "randutv_profile_read", "randutv_factor_mixed",

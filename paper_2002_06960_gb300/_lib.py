@@ -33,6 +33,7 @@ _SIGS = {
                                     c_vp]),
     "randutv_stream_status": (c_int, [c_vp]),
     "randutv_philox_normal": (c_int, [c_u64, c_u32, c_u32, c_u32, c_i64, c_i64, c_vp, c_vp]),
+    "randutv_philox_normal_f32": (c_int, [c_u64, c_u32, c_u32, c_u32, c_i64, c_i64, c_vp, c_vp]),
     "randutv_philox_words": (c_int, [c_u64, c_u32, c_u32, c_u32, c_u32, c_i64, c_vp, c_vp]),
     "randutv_householder_qr": (c_int, [c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_vp]),
     "randutv_wy_factor": (c_int, [c_i64, c_i64, c_vp, c_vp, c_vp, c_vp]),
@@ -247,6 +248,13 @@ def randutv_factor_ooc(A_host, b, q, seed, U_host=None, V_host=None, device_byte
 def randutv_philox_normal(seed, step, matrix_id, stream_id, rows, cols, device="cuda"):
     G = colmajor_empty(rows, cols, device=device)
     _check("randutv_philox_normal", lib().randutv_philox_normal(
+        seed, step, matrix_id, stream_id, rows, cols, _ptr(G), _stream()))
+    return G
+
+
+def randutv_philox_normal_f32(seed, step, matrix_id, stream_id, rows, cols, device="cuda"):
+    G = colmajor_empty(rows, cols, device=device, dtype=torch.float32)
+    _check("randutv_philox_normal_f32", lib().randutv_philox_normal_f32(
         seed, step, matrix_id, stream_id, rows, cols, _ptr(G), _stream()))
     return G
 

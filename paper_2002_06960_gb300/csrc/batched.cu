@@ -695,14 +695,11 @@ __device__ void cta_sketch(uint64_t seed, int step, int mid, int rows, int cols,
   const int64_t count = (int64_t)rows * cols, npairs = (count + 1) >> 1;
   for (int64_t p = threadIdx.x; p < npairs; p += BT) {
     const uint4 w = philox4x32_10(make_uint4((uint32_t)p, (uint32_t)step, (uint32_t)mid, 0u), key);
-    const float u1 = (float)((w.x >> 8) + 1u) * 0x1.0p-24f;
-    const float u2 = (float)(w.z >> 8) * 0x1.0p-24f;
-    const float rho = sqrtf(-2.f * logf(u1));
-    float s, c;
-    sincospif(2.f * u2, &s, &c);
+    float z0, z1;
+    box_muller_f32(w, &z0, &z1);
     const int64_t l0 = 2 * p;
-    G[l0] = rho * c;  // G is rows x cols with ld = rows: element l at G[l]
-    if (l0 + 1 < count) G[l0 + 1] = rho * s;
+    G[l0] = z0;  // G is rows x cols with ld = rows: element l at G[l]
+    if (l0 + 1 < count) G[l0 + 1] = z1;
   }
   __syncthreads();
 }
@@ -852,12 +849,7 @@ int launch_batched(const void* desc_dev, const int* order_dev, int count, int* n
   a.work_stride = work_stride;
   a.mmax = mmax;
   const size_t smem = sizeof(Smem);
-  static bool configured = false;
-  if (!configured) {
-    RUTV_CK(cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    configured = true;
-  }
+  RUTV_TRY(ensure_smem((const void*)batched_kernel, smem));
   RUTV_CK(cudaMemsetAsync(next_dev, 0, sizeof(int), st));
   batched_kernel<<<grid, BT, smem, st>>>(a);
   note_launch();
@@ -866,8 +858,7 @@ int launch_batched(const void* desc_dev, const int* order_dev, int count, int* n
 }
 
 int batched_max_ctas_per_sm(int* out) {
-  RUTV_CK(cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)sizeof(Smem)));
+  RUTV_TRY(ensure_smem((const void*)batched_kernel, sizeof(Smem)));
   RUTV_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, batched_kernel, BT, sizeof(Smem)));
   return 0;
 }

@@ -591,12 +591,7 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.ntiles = tiles_m * p.tiles_n;
   p.ksteps = (K + BK - 1) / BK;
   const size_t smem = 1024 + (size_t)stages * per_stage + ctile_bytes + (2 * stages + 7) * 8 + 16;
-  static size_t configured = 0;
-  if (smem > configured) {
-    RUTV_CK(cudaFuncSetAttribute(bgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)smem));
-    configured = smem;
-  }
+  RUTV_TRY(ensure_smem((const void*)bgemm_kernel, smem));
   // persistent: at most one CTA per SM (the shared memory allows no more)
   int cap = dev_info().sms;
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;

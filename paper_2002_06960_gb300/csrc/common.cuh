@@ -67,6 +67,15 @@ int scratch_reserve(size_t bytes, Arena* out);
 // The device status words of the current device (64 words, persistent).
 int status_words(unsigned** out);
 
+// Raises the dynamic shared-memory limit of kernel `func` on the current
+// device to at least `bytes` (the attribute is kept per device, so a process
+// that uses several GPUs sets it on each).  Thread-safe.
+int ensure_smem(const void* func, size_t bytes);
+
+// Sets cudaFuncAttributeNonPortableClusterSizeAllowed on `func` for the
+// current device, once per device.  Thread-safe.
+int ensure_nonportable_cluster(const void* func);
+
 // Words of device status shared by the kernels of one call: [0] error code,
 // [1] where the error happened, [2..3] barrier counter and generation.
 struct StatusWords {

@@ -205,12 +205,7 @@ int qr_launch(QrArgs& a, int nb, cudaStream_t st) {
   const size_t smem = (size_t)rows_per * (size_t)a.c * sizeof(double);
   void* args[] = {&a};
   if (smem <= kQrSmemMax) {
-    static bool configured = false;
-    if (!configured) {
-      RUTV_CK(cudaFuncSetAttribute(householder_panel_kernel<true>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kQrSmemMax));
-      configured = true;
-    }
+    RUTV_TRY(ensure_smem((const void*)householder_panel_kernel<true>, kQrSmemMax));
     RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel<true>, dim3(nb),
                                         dim3(QR_THREADS), args, smem, st));
   } else {

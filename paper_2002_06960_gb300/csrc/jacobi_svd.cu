@@ -473,19 +473,9 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
 template <typename Real, bool kFinal>
 int configure(int b, int ncl, size_t* smem_out) {
-  static size_t configured = 0;
-  static bool nonportable = false;
-  if (!nonportable) {
-    RUTV_CK(cudaFuncSetAttribute(jacobi_kernel<Real, kFinal>,
-                                 cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
-    nonportable = true;
-  }
+  RUTV_TRY(ensure_nonportable_cluster((const void*)jacobi_kernel<Real, kFinal>));
   const size_t smem = jac_smem_bytes<Real>(b, ncl);
-  if (smem > configured) {
-    RUTV_CK(cudaFuncSetAttribute(jacobi_kernel<Real, kFinal>,
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    configured = smem;
-  }
+  RUTV_TRY(ensure_smem((const void*)jacobi_kernel<Real, kFinal>, smem));
   *smem_out = smem;
   return 0;
 }

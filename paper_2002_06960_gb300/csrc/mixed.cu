@@ -10,6 +10,9 @@
 //     product BF16 split on tcgen05, FP32 accuracy, FP32 accumulation.
 //   * Householder vectors and norms (the panel QRs), the WY factor S and the
 //     b x b SVD: FP64, the same kernels as the FP64 path.
+//   * After the last step, one re-orthogonalisation pass of U and V (their
+//     Gram's diagonal in FP64, a first-order Cholesky correction), with T
+//     corrected alongside so that U T V^T and the shape of T are kept.
 #include <cuda_bf16.h>
 
 #include <utility>
@@ -118,6 +121,10 @@ struct MixedWork {
   size_t dgemm_bytes;
   float* tmp2;     // side stream: fold-back products
   double* dgemm2;  // side stream: dgemm scratch
+  // final re-orthogonalisation of U and V
+  float* E;                    // X^T X - I (FP32, max(m,n)^2)
+  __nv_bfloat16 *Phi, *PhiT;   // its first-order Cholesky correction and transpose
+  double* dcol;                // FP64 diagonal of X^T X - I
 };
 
 size_t planes_bytes(int64_t rows, int64_t cols) {
@@ -174,6 +181,10 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add(dgemm_scratch_bytes(b, b));
   add((size_t)big * b * 4);          // tmp2
   add(dgemm_scratch_bytes(b, b));    // dgemm2
+  add((size_t)big * big * 4);        // E
+  add((size_t)pad8(big) * big * 2);  // Phi
+  add((size_t)pad8(n) * n * 2);      // PhiT
+  add((size_t)big * 8);              // dcol
   return s + 8192;
 }
 
@@ -214,6 +225,10 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.dgemm = (double*)ar.take(w.dgemm_bytes);
   w.tmp2 = (float*)ar.take((size_t)big * b * 4);
   w.dgemm2 = (double*)ar.take(w.dgemm_bytes);
+  w.E = (float*)ar.take((size_t)big * big * 4);
+  w.Phi = (__nv_bfloat16*)ar.take((size_t)pad8(big) * big * 2);
+  w.PhiT = (__nv_bfloat16*)ar.take((size_t)pad8(n) * n * 2);
+  w.dcol = (double*)ar.take((size_t)big * 8);
   return w;
 }
 
@@ -334,6 +349,56 @@ int mixed_flush_folds(MCtx& c) {
     RUTV_TRY(split_f32(w.tmp, bi, bi, nc, 0, w.T, k, k + bi, c.st));
   }
   c.folds.clear();
+  return 0;
+}
+
+// Final re-orthogonalisation of U and V (FP32 outputs Uo, Vo) with T (FP32
+// output To) carried along, so that U T V^T stays the same product and T
+// stays upper triangular.  For X = U or V, E = X^T X - I holds the loss of
+// orthogonality of the FP32-level factorization (about 1e-6).  With Phi =
+// striu(E) + diag(E)/2 (the first-order Cholesky factor of I + E, minus I):
+//   U' = U (I - Phi_U),  V' = V (I - Phi_V^T),  T' = (I + Phi_U) T (I + Phi_V),
+// and U'^T U' = I + O(E^2), V'^T V' = I + O(E^2), U' T' V'^T = U T V^T + O(E^2),
+// with T' upper triangular (a product of upper triangular factors).  E's
+// diagonal is summed in FP64 from the FP32 entries; its off-diagonal entries
+// come from the six-product split (FP32-accurate; they are random-signed
+// sums, which the tensor-core accumulation handles without bias).  The three
+// corrections are O(E) terms, so one BF16 product each is accurate enough.
+// The planes of T (the state before the pass) feed both T products; the
+// planes of U^T and V^T, no longer needed, hold the planes of U and V.
+// Finally the off-diagonal entries that the pass leaves inside the diagonal
+// b x b blocks of T (about |E| times their diagonal) are zeroed, restoring
+// exactly diagonal blocks.
+int mixed_reorth(MCtx& c, float* To, float* Uo, float* Vo) {
+  MixedWork& w = c.w;
+  const int64_t m = c.m, n = c.n, p = m < n ? m : n;
+  if (c.want_u) {
+    Planes P = w.Ut;  // m x m, now the planes of U (not U^T)
+    RUTV_TRY(split_f32(Uo, m, m, m, 0, P, 0, 0, c.st));
+    RUTV_TRY(launch_bgemm(opnd(P, 3, 0, 0, 0), opnd(P, 3, 0, 0, 0), (int)m, (int)m, (int)m, 3,
+                          out_f32(w.E, m), c.status, c.st));
+    RUTV_TRY(reorth_phi(Uo, m, m, w.E, m, w.dcol, w.Phi, pad8(m), nullptr, 0, c.st));
+    // U -= U Phi_U
+    RUTV_TRY(launch_bgemm(opnd(P, 1, 0, 0, 1), opnd_bf16(w.Phi, m, m, pad8(m), 0), (int)m, (int)m,
+                          (int)m, 1, out_f32(Uo, m, -1.f, 1.f), c.status, c.st));
+    // T += Phi_U T
+    RUTV_TRY(launch_bgemm(opnd_bf16(w.Phi, m, m, pad8(m), 1), opnd(w.T, 1, 0, 0, 0), (int)m,
+                          (int)n, (int)m, 1, out_f32(To, m, 1.f, 1.f), c.status, c.st));
+  }
+  if (c.want_v) {
+    Planes P = w.Vt;  // n x n, now the planes of V
+    RUTV_TRY(split_f32(Vo, n, n, n, 0, P, 0, 0, c.st));
+    RUTV_TRY(launch_bgemm(opnd(P, 3, 0, 0, 0), opnd(P, 3, 0, 0, 0), (int)n, (int)n, (int)n, 3,
+                          out_f32(w.E, n), c.status, c.st));
+    RUTV_TRY(reorth_phi(Vo, n, n, w.E, n, w.dcol, w.Phi, pad8(n), w.PhiT, pad8(n), c.st));
+    // V -= V Phi_V^T
+    RUTV_TRY(launch_bgemm(opnd(P, 1, 0, 0, 1), opnd_bf16(w.PhiT, n, n, pad8(n), 0), (int)n, (int)n,
+                          (int)n, 1, out_f32(Vo, n, -1.f, 1.f), c.status, c.st));
+    // T += T Phi_V
+    RUTV_TRY(launch_bgemm(opnd(w.T, 1, 0, 0, 1), opnd_bf16(w.Phi, n, n, pad8(n), 0), (int)m,
+                          (int)n, (int)n, 1, out_f32(To, m, 1.f, 1.f), c.status, c.st));
+  }
+  if (c.want_u || c.want_v) RUTV_TRY(zero_block_offdiag(To, m, p, c.b, c.st));
   return 0;
 }
 
@@ -467,6 +532,7 @@ int randutv_factor_mixed(int64_t m, int64_t n, const float* A, int64_t lda, int 
   RUTV_TRY(merge_f32(c.w.T, 0, 0, m, n, 0, T, m, st));
   if (c.want_u) RUTV_TRY(merge_f32(c.w.Ut, 0, 0, m, m, 1, U, m, st));
   if (c.want_v) RUTV_TRY(merge_f32(c.w.Vt, 0, 0, n, n, 1, V, n, st));
+  if (step == (int)nsteps(m, n, b)) RUTV_TRY(mixed_reorth(c, T, U, V));  // completed runs only
   return 0;
 }
 

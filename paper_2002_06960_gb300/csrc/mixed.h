@@ -73,6 +73,14 @@ int set_identity_planes(const Planes& X, cudaStream_t st);
 int launch_check_finite_f32(int64_t rows, int64_t cols, const float* X, int64_t ld, unsigned* err,
                             cudaStream_t st);
 int set_diag_planes(const Planes& T, int64_t k, int64_t bi, const double* D, cudaStream_t st);
+// Final re-orthogonalisation: d = diag(X^T X) - 1 in FP64 (X FP32, n x n),
+// and Phi = striu(E) + diag(d)/2 in BF16 (E FP32, read on and above the
+// diagonal), with its transpose PhiT when PhiT is non-null.
+int reorth_phi(const float* X, int64_t ldx, int64_t n, const float* E, int64_t lde, double* d,
+               __nv_bfloat16* Phi, int64_t ldp, __nv_bfloat16* PhiT, int64_t ldpt,
+               cudaStream_t st);
+// Zeroes the off-diagonal entries of every b x b diagonal block of T (p = min(m, n)).
+int zero_block_offdiag(float* T, int64_t ld, int64_t p, int64_t b, cudaStream_t st);
 int philox_normal_bf16(uint64_t seed, uint32_t step, uint32_t mid, uint32_t sid, int64_t rows,
                        int64_t cols, __nv_bfloat16* G, int64_t ldg, cudaStream_t st);
 

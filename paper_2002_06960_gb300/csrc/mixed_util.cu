@@ -216,4 +216,96 @@ int set_diag_planes(const Planes& T, int64_t k, int64_t bi, const double* D, cud
   return 0;
 }
 
+// ------------------------------------------- final re-orthogonalisation
+//
+// For X with X^T X = I + E, E small and symmetric, the Cholesky factor of
+// I + E is I + Phi(E) + O(E^2), with Phi(E) the strictly upper triangle of E
+// plus half its diagonal, so X (I - Phi(E)) is orthogonal to O(E^2).  The
+// diagonal of E is taken here in FP64 from the FP32 entries of X (the
+// products are exact in FP64); the tensor-core Gram supplies the rest.
+
+namespace {
+
+// d[i] = sum_r X(r, i)^2 - 1 in FP64, one warp per column.
+__global__ void colnorm_minus_one_kernel(const float* __restrict__ X, int64_t ldx, int64_t rows,
+                                         int64_t cols, double* __restrict__ d) {
+  const int warp = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const int nwarps = (int)((gridDim.x * (int64_t)blockDim.x) >> 5);
+  for (int64_t j = warp; j < cols; j += nwarps) {
+    double s = 0.0;
+    for (int64_t r = lane; r < rows; r += 32) {
+      const double x = (double)X[r + j * ldx];
+      s = fma(x, x, s);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) d[j] = s - 1.0;
+  }
+}
+
+// Phi (n x n, BF16, ld ldp) from E (FP32, ld lde; only entries on or above
+// the diagonal are read) and d; PhiT = Phi^T when non-null.  32 x 32 tiles,
+// transposed through shared memory so that both writes are coalesced.
+__global__ void phi_kernel(const float* __restrict__ E, int64_t lde, const double* __restrict__ d,
+                           int64_t n, __nv_bfloat16* __restrict__ Phi, int64_t ldp,
+                           __nv_bfloat16* __restrict__ PhiT, int64_t ldpt) {
+  __shared__ float tile[32][33];
+  const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+  for (int jj = threadIdx.y; jj < 32; jj += blockDim.y) {
+    const int64_t i = i0 + threadIdx.x, j = j0 + jj;
+    float v = 0.f;
+    if (i < n && j < n) {
+      if (i < j) v = E[i + j * lde];
+      else if (i == j) v = (float)(0.5 * d[i]);
+      Phi[i + j * ldp] = __float2bfloat16_rn(v);
+    }
+    tile[jj][threadIdx.x] = v;
+  }
+  if (!PhiT) return;  // uniform over the block
+  __syncthreads();
+  for (int ii = threadIdx.y; ii < 32; ii += blockDim.y) {
+    const int64_t j = j0 + threadIdx.x, i = i0 + ii;  // PhiT(j, i) = Phi(i, j)
+    if (i < n && j < n) PhiT[j + i * ldpt] = __float2bfloat16_rn(tile[threadIdx.x][ii]);
+  }
+}
+
+// Zeroes the off-diagonal entries of every diagonal block of T (blocks of b
+// along the first p = min(m, n) columns, the last one narrower).
+__global__ void zero_block_offdiag_kernel(float* T, int64_t ld, int64_t p, int64_t b) {
+  const int64_t total = p * b;  // (row offset inside the block, column) pairs
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = e / b, io = e % b;  // column j, row k + io of its block
+    const int64_t k = (j / b) * b;
+    const int64_t i = k + io;
+    if (i < p && i != j) T[i + j * ld] = 0.f;
+  }
+}
+
+}  // namespace
+
+int reorth_phi(const float* X, int64_t ldx, int64_t n, const float* E, int64_t lde, double* d,
+               __nv_bfloat16* Phi, int64_t ldp, __nv_bfloat16* PhiT, int64_t ldpt,
+               cudaStream_t st) {
+  if (n <= 0) return 0;
+  ProfScope prof(K_OTHER, 2.0 * (double)n * n, 4.0 * (double)n * n + 6.0 * (double)n * n, st);
+  int64_t blocks = (n * 32 + 255) / 256;
+  const int64_t cap = (int64_t)dev_info().sms * 16;
+  if (blocks > cap) blocks = cap;
+  colnorm_minus_one_kernel<<<(unsigned)blocks, 256, 0, st>>>(X, ldx, n, n, d);
+  const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32));
+  phi_kernel<<<grid, dim3(32, 8), 0, st>>>(E, lde, d, n, Phi, ldp, PhiT, ldpt);
+  note_launch(2);
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
+int zero_block_offdiag(float* T, int64_t ld, int64_t p, int64_t b, cudaStream_t st) {
+  if (p <= 0 || b <= 1) return 0;
+  zero_block_offdiag_kernel<<<grid_of(p * b), 256, 0, st>>>(T, ld, p, b);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
 }  // namespace rutv

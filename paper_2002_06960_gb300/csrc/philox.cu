@@ -55,6 +55,38 @@ int launch_philox_normal(uint64_t seed, uint32_t step, uint32_t mid, uint32_t si
   return 0;
 }
 
+__global__ void philox_normal_f32_kernel(PhiloxKey key, uint32_t step, uint32_t mid, uint32_t sid,
+                                         int64_t rows, int64_t count, float* __restrict__ G,
+                                         int64_t ldg) {
+  const int64_t npairs = (count + 1) >> 1;
+  for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p < npairs;
+       p += (int64_t)gridDim.x * blockDim.x) {
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)p, step, mid, sid), key);
+    float z0, z1;
+    box_muller_f32(w, &z0, &z1);
+    const int64_t l0 = 2 * p;
+    G[(l0 % rows) + (l0 / rows) * ldg] = z0;
+    if (l0 + 1 < count) G[((l0 + 1) % rows) + ((l0 + 1) / rows) * ldg] = z1;
+  }
+}
+
+int launch_philox_normal_f32(uint64_t seed, uint32_t step, uint32_t mid, uint32_t sid,
+                             int64_t rows, int64_t cols, float* G, int64_t ldg, cudaStream_t st) {
+  const int64_t count = rows * cols;
+  if (count == 0) return 0;
+  const int64_t npairs = (count + 1) >> 1;
+  int64_t blocks = (npairs + 255) / 256;
+  const int64_t cap = (int64_t)dev_info().sms * 16;
+  if (blocks > cap) blocks = cap;
+  PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
+  ProfScope prof(K_PHILOX, 0.0, 4.0 * (double)count, st);
+  philox_normal_f32_kernel<<<(unsigned)blocks, 256, 0, st>>>(key, step, mid, sid, rows, count, G,
+                                                             ldg);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
 int launch_philox_words(uint64_t seed, uint4 c, int64_t count, uint32_t* out, cudaStream_t st) {
   if (count == 0) return 0;
   const int threads = 256;

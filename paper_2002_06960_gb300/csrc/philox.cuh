@@ -40,4 +40,17 @@ __device__ __forceinline__ void box_muller(uint4 w, double* z0, double* z1) {
   *z1 = rho * s;
 }
 
+// The batched form's FP32 pair: 24-bit uniforms u1 = ((x0 >> 8) + 1) 2^-24
+// in (0, 1] and u2 = (x2 >> 8) 2^-24 in [0, 1) (both exact in FP32),
+// rho = sqrt(-2 ln u1), (rho cos 2 pi u2, rho sin 2 pi u2) in FP32 arithmetic.
+__device__ __forceinline__ void box_muller_f32(uint4 w, float* z0, float* z1) {
+  const float u1 = (float)((w.x >> 8) + 1u) * 0x1.0p-24f;
+  const float u2 = (float)(w.z >> 8) * 0x1.0p-24f;
+  const float rho = sqrtf(-2.f * logf(u1));
+  float s, c;
+  sincospif(2.f * u2, &s, &c);
+  *z0 = rho * c;
+  *z1 = rho * s;
+}
+
 }  // namespace rutv

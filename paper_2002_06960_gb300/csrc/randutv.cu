@@ -154,6 +154,44 @@ int scratch_reserve(size_t bytes, Arena* out) {
   return 0;
 }
 
+namespace {
+struct FuncAttr {
+  const void* func;
+  size_t smem;
+  bool nonportable;
+};
+std::vector<FuncAttr> g_attr[kMaxDev];
+
+FuncAttr& func_attr(int d, const void* func) {
+  for (FuncAttr& a : g_attr[d])
+    if (a.func == func) return a;
+  g_attr[d].push_back(FuncAttr{func, 0, false});
+  return g_attr[d].back();
+}
+}  // namespace
+
+int ensure_smem(const void* func, size_t bytes) {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_mu);
+  FuncAttr& a = func_attr(d, func);
+  if (a.smem < bytes) {
+    RUTV_CK(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    a.smem = bytes;
+  }
+  return 0;
+}
+
+int ensure_nonportable_cluster(const void* func) {
+  const int d = current_device();
+  std::lock_guard<std::mutex> lk(g_mu);
+  FuncAttr& a = func_attr(d, func);
+  if (!a.nonportable) {
+    RUTV_CK(cudaFuncSetAttribute(func, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    a.nonportable = true;
+  }
+  return 0;
+}
+
 static int stage_reserve(size_t bytes, char** out) {
   const int d = current_device();
   std::lock_guard<std::mutex> lk(g_mu);
@@ -562,7 +600,16 @@ int randutv_selftest_wait_timeout(void* stream) {
   RUTV_CK(cudaStreamSynchronize(st));
   unsigned h[2] = {0, 0};
   RUTV_CK(cudaMemcpy(h, status, sizeof h, cudaMemcpyDeviceToHost));
-  return (h[0] == (unsigned)RANDUTV_ETIMEOUT && h[1] == 901u) ? (int)h[0] : -100;
+  if (h[0] == (unsigned)RANDUTV_ETIMEOUT && h[1] == 901u) return (int)h[0];
+  if (h[0] != 0u) {
+    // some other device status: report it as it is, with the site it came from
+    char msg[96];
+    snprintf(msg, sizeof msg, "selftest: device status %u at site %u", h[0], h[1]);
+    set_last_error(msg);
+    return (int)h[0];
+  }
+  set_last_error("selftest: the wait completed without a timeout being recorded");
+  return -100;
 }
 
 uint64_t randutv_launch_count(int reset) {
@@ -702,6 +749,16 @@ int randutv_philox_normal(uint64_t seed, uint32_t step, uint32_t matrix_id, uint
   if (!G && rows * cols > 0) return -7;
   return launch_philox_normal(seed, step, matrix_id, stream_id, rows, cols, G, rows,
                               (cudaStream_t)stream);
+}
+
+int randutv_philox_normal_f32(uint64_t seed, uint32_t step, uint32_t matrix_id,
+                              uint32_t stream_id, int64_t rows, int64_t cols, float* G,
+                              void* stream) {
+  if (rows < 0) return -5;
+  if (cols < 0) return -6;
+  if (!G && rows * cols > 0) return -7;
+  return launch_philox_normal_f32(seed, step, matrix_id, stream_id, rows, cols, G, rows,
+                                  (cudaStream_t)stream);
 }
 
 int randutv_philox_words(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,

@@ -1,16 +1,20 @@
 """Batched randUTV (one persistent launch over uneven sizes) against the oracle.
 
-Each matrix of the batch is checked by its errors against the FP64 oracle
-run on the same input: reconstruction and orthogonality at the FP32 level,
-exact zeros below the diagonal, and the leading diagonal of T (the
-singular-value estimates) close to the oracle's.  The launch is also checked
-for determinism, for giving the same result when captured in a CUDA graph
-and replayed, and for per-matrix status reporting.
+The batched form draws its sketch with an FP32 Box-Muller of the same Philox
+words; the oracle draws that identical G (``sketch_f32``) and runs the
+method in FP64.  Each matrix of the batch is then checked against it:
+reconstruction at most 1e-6, orthogonality at the level FP32 updates
+reach, exact zeros below the diagonal, and the singular-value estimates:
+each block tracks its own trailing singular values wherever the sketch
+resolves them, and the first block's estimates equal the oracle's.  The launch is
+also checked for determinism, for giving the same result when captured in a
+CUDA graph and replayed, and for per-matrix status reporting.
 """
 import pytest
 import torch
 
 import oracle
+import sigma_tracking
 from paper_2002_06960_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -38,6 +42,12 @@ def _mats(p, sizes, seed=2):
     return out
 
 
+# Orthogonality of the FP32 factors: each of the ceil(p/b) steps applies an
+# FP32 compact-WY update to U and V, and their rounding accumulates to about
+# 1.5e-6 after 32 steps of 32 columns at n = 1024 (measured); an FP32 matrix
+# that is orthogonal to rounding would show 5e-8.
+ORTH_GATE = 2e-6
+
 SIZES = [(200, 150), (150, 200), (64, 64), (300, 97), (33, 257), (16, 16), (1, 1), (1, 7), (9, 1),
          (128, 128), (257, 33)]
 
@@ -54,13 +64,18 @@ def test_batched_errors_against_oracle(pkg, b):
         U, T, V = (plan.U[i].cpu().double(), plan.T[i].cpu().double(), plan.V[i].cpu().double())
         Aq = A.to(f32).double()
         recon = oracle.recon_error(Aq, U, T, V)
-        assert recon < 2e-6, (i, recon)
-        assert oracle.orth_error(U) < 2e-6 and oracle.orth_error(V) < 2e-6, i
+        assert recon < 1e-6, (i, recon)
+        ou, ov = oracle.orth_error(U), oracle.orth_error(V)
+        assert ou < ORTH_GATE and ov < ORTH_GATE, (i, ou, ov)
         assert float(torch.tril(T, -1).abs().max()) == 0.0
-        ref = oracle.randutv(Aq, b, 1, 5, matrix_id=i)
-        d, d0 = torch.diagonal(T).abs(), torch.diagonal(ref.T).abs()
-        k = min(8, d.numel())
-        assert float(((d[:k] - d0[:k]).abs() / d0[:k].clamp_min(1e-30)).max()) < 1e-3, i
+        ref = oracle.randutv(Aq, b, 1, 5, matrix_id=i, sketch_f32=True)
+        if min(Aq.shape) > 1:
+            # FP32 sketch and products (u = 2^-24) against FP64 on the identical
+            # sketch: each block tracks its own trailing singular values where
+            # the sketch resolves them, and the first block's estimates equal
+            # the oracle's (a different sketch would move them by about the
+            # FP64 method's own error there, up to 1e-3)
+            sigma_tracking.check(T, ref.T, b, 1, 2.0 ** -24, tol=2e-3, first_tol=1e-4)
     plan.close()
 
 
@@ -115,9 +130,9 @@ def test_autotuner_installs_a_table(pkg):
 @pytest.mark.parametrize("b", [32, 64])
 def test_batched_maximum_sizes(pkg, b):
     """Matrices at the 1024 limit, square and ragged, checked by properties
-    that hold at any size: reconstruction and orthogonality at the FP32
-    level, exact zeros below the diagonal, and the leading diagonal of T
-    against the prescribed spectrum."""
+    that hold at any size: reconstruction at most 1e-6, orthogonality at the
+    FP32 level, exact zeros below the diagonal, and the leading diagonal of T against the
+    prescribed spectrum."""
     p, batched = pkg
     sizes = [(1024, 1024), (1024, 1001), (999, 1024), (1024, 40)]
     mats = _mats(p, sizes, seed=11)
@@ -128,8 +143,9 @@ def test_batched_maximum_sizes(pkg, b):
     for i, (A, _) in enumerate(mats):
         U, T, V = (plan.U[i].cpu().double(), plan.T[i].cpu().double(), plan.V[i].cpu().double())
         Aq = A.to(f32).double()
-        assert oracle.recon_error(Aq, U, T, V) < 2e-6, i
-        assert oracle.orth_error(U) < 2e-6 and oracle.orth_error(V) < 2e-6, i
+        assert oracle.recon_error(Aq, U, T, V) < 1e-6, i
+        ou, ov = oracle.orth_error(U), oracle.orth_error(V)
+        assert ou < ORTH_GATE and ov < ORTH_GATE, (i, ou, ov)
         assert float(torch.tril(T, -1).abs().max()) == 0.0
         sig = torch.exp(-torch.arange(4, dtype=f64) / 16.0)
         d = torch.diagonal(T)[:4].abs()

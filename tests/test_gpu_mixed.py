@@ -4,13 +4,16 @@ The GEMM is checked against an FP64 product of the same operands: with one
 BF16 plane, against the product of the BF16-rounded inputs (so only the FP32
 accumulation differs); with three planes, against the exact product (the
 split is FP32-accurate).  The factorization is checked by its errors against
-the FP64 oracle: reconstruction, orthogonality, exact zeros, and the
-diagonal of T (the singular-value estimates).
+the FP64 oracle: reconstruction (at most 1e-6), orthogonality after the
+final re-orthogonalisation (at most 1e-7), exact zeros, and the diagonal of
+T (the singular-value estimates) wherever the BF16 sketch resolves it (see
+tests/sigma_tracking.py).
 """
 import pytest
 import torch
 
 import oracle
+import sigma_tracking
 from paper_2002_06960_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -83,23 +86,22 @@ def test_mixed_factorization_errors(pkg, kind, m, n, b, q):
     U, T, V = _mixed(pkg, A, b, q, 0)
     recon = oracle.recon_error(A, U, T, V)
     ou, ov = oracle.orth_error(U), oracle.orth_error(V)
-    assert recon < 1e-5, recon
-    assert ou < 1e-5 and ov < 1e-5, (ou, ov)
+    # after the final re-orthogonalisation U and V are orthogonal to about the
+    # rounding of their FP32 entries (sqrt(2/3) 2^-24 = 5e-8 for an exactly
+    # orthogonal matrix), and U T V^T reproduces A to the FP32-level target
+    assert recon < 1e-6, recon
+    assert ou < 1e-7 and ov < 1e-7, (ou, ov)
     assert float(torch.tril(T, -1).abs().max()) == 0.0
+    p = min(m, n)
+    for k in range(0, p, b):   # every diagonal block is exactly diagonal
+        bi = min(b, p - k)
+        blk = T[k:k + bi, k:k + bi]
+        assert float((blk - torch.diag(torch.diagonal(blk))).abs().max()) == 0.0
     ref = oracle.randutv(A, b, q, 0)
-    d, d0 = torch.diagonal(T).abs(), torch.diagonal(ref.T).abs()
-    # The leading singular-value estimates agree with the FP64 oracle's.  The
-    # BF16 sketch cannot resolve directions of T22 below its rounding level
-    # (about 2^-9 ||T22||), so deeper estimates in each block may differ from
-    # the FP64 run; they are still estimates of the same spectrum.
-    rel = (d - d0).abs() / d0
-    assert float(rel[:16].max()) < 1e-4
-    assert float(rel[:b // 2].max()) < 1e-2
-    # everywhere above the sketch's BF16 resolution the estimates stay within
-    # a factor of two of the FP64 run's
-    top = d0 > 1e-3 * d0[0]
-    ratio = (d / d0)[top]
-    assert float(ratio.max()) < 2.0 and float(ratio.min()) > 0.5, (ratio.min(), ratio.max())
+    # BF16 sketch and power products (u = 2^-8): each block tracks its own
+    # trailing singular values where the sketch resolves them, and the first
+    # block's resolved estimates equal the FP64 oracle's
+    sigma_tracking.check(T, ref.T, b, q, 2.0 ** -8, tol=1e-2, first_tol=1e-4)
 
 
 def test_mixed_single_block_is_svd(pkg):
@@ -122,8 +124,8 @@ def test_mixed_one_ragged_block(pkg, m, n, b):
     A = inputs.matrix("exp16", m, n, seed=4)
     U, T, V = _mixed(pkg, A, b, 1, 0)
     p = min(m, n)
-    assert oracle.recon_error(A, U, T, V) < 2e-6
-    assert oracle.orth_error(U) < 2e-6 and oracle.orth_error(V) < 2e-6
+    assert oracle.recon_error(A, U, T, V) < 1e-6
+    assert oracle.orth_error(U) < 1e-7 and oracle.orth_error(V) < 1e-7
     assert float(torch.tril(T, -1).abs().max()) == 0.0
     sig = torch.linalg.svdvals(A)
     d = torch.diagonal(T)[:p].abs()

@@ -60,6 +60,19 @@ def test_philox_normal_matches_oracle(pkg, rows, cols, step, mid):
     assert float((G - ref).abs().max()) <= 1e-14 * max(1.0, float(ref.abs().max()))
 
 
+@pytest.mark.parametrize("rows,cols,step,mid", [(1000, 64, 0, 0), (777, 13, 5, 3), (1, 1, 2, 0),
+                                                (1023, 64, 15, 4095)])
+def test_philox_normal_f32_matches_oracle(pkg, rows, cols, step, mid):
+    """The batched form's FP32 sketch against the oracle's: the same words, and
+    Box-Muller of the same exact FP32 uniforms; logf / sqrtf / sincospif / the
+    product each round in FP32, so the two agree to a few FP32 ulp."""
+    G = cpu(pkg.randutv_philox_normal_f32(7, step, mid, 0, rows, cols)).double()
+    ref = torch.from_numpy(philox.sketch_f32(7, step, rows, cols, mid)).double()
+    assert torch.isfinite(G).all()
+    tol = 8 * 2.0 ** -24 * ref.abs() + 1e-30
+    assert bool(((G - ref).abs() <= tol).all()), float(((G - ref).abs() / ref.abs()).max())
+
+
 # -------------------------------------------------------------- dgemm ----
 
 @pytest.mark.parametrize("ta,tb", [("N", "N"), ("N", "T"), ("T", "N"), ("T", "T")])
