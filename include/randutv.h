@@ -319,6 +319,39 @@ int randutv_dgemm(char transa, char transb, int64_t M, int64_t N, int64_t K, dou
                   const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
                   double* C, int64_t ldc, void* stream);
 
+/* ------------------------------------------------------ randUTV by blocks --
+ * The analyzer of §3.2.4: the task list of randUTV_AB for an m x n matrix in
+ * blocks of b (tile starts: multiples of b up to p = min(m, n), then p + b t),
+ * q power iterations, with U (want_u) and V (want_v) or not.  Each task is an
+ * operation (randutv_ab_op_name) of one block step, with up to four blocks
+ * read and four written.  A block is kind << 40 | i << 20 | j, kind 0..9 =
+ * A, G, Y, Z, B, C, P, Q, U, V (A holds T as it is formed; G, Y, Z the tiles of
+ * the sketch and its products; B, C the compact-WY factors of the QRs of the
+ * Y tiles and of the A tiles of the block column; P, Q the factors U_s, V_s
+ * of the step's small SVD).  Host code only; no device is touched.
+ *   ops, steps (cap ints each), operands (8 * cap: in[0..3], out[0..3],
+ *   -1 where unused): HOST arrays, filled for the first min(cap, count)
+ *   tasks; any may be NULL.  Returns the number of tasks, or -i for a bad
+ *   argument i (m, n, b >= 1; 0 <= q <= 16). */
+int64_t randutv_ab_tasks(int64_t m, int64_t n, int b, int q, int want_u, int want_v, int32_t* ops,
+                         int32_t* steps, int64_t* operands, int64_t cap);
+
+/* Name of an operation of the task list ("Comp_td_QR", ...). */
+const char* randutv_ab_op_name(int op);
+
+/* I/O of the dispatchers of §3.2.4 on the first max_tasks tasks (all when
+ * negative) of that list, with every block held in an external store:
+ * cache_blocks == 0 is the traditional dispatcher (per task, every input
+ * block read and every output block written); cache_blocks > 0 keeps that
+ * many blocks with least-recently-used replacement (ties: lowest slot),
+ * writing a replaced block back only when it was modified.  reads, writes:
+ * HOST int64 outputs.  trace (HOST, max_tasks * cache_blocks, or NULL): the
+ * block in every slot after each task (-1 = empty).  Returns 0, -i for a
+ * bad argument, or RANDUTV_EUNSUPPORTED when one task needs more blocks than
+ * the cache holds. */
+int randutv_ab_io(int64_t m, int64_t n, int b, int q, int want_u, int want_v, int64_t max_tasks,
+                  int64_t cache_blocks, int64_t* reads, int64_t* writes, int64_t* trace);
+
 /* ------------------------------------------------------------- utilities -- */
 
 /* Bytes of library scratch one factorization of this shape needs. */

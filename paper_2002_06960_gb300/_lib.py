@@ -65,6 +65,10 @@ _SIGS = {
     "randutv_lowrank": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64, c_vp, c_vp]),
     "randutv_lowrank_backward": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64,
                                          c_vp, c_vp, c_vp]),
+    "randutv_ab_tasks": (c_i64, [c_i64, c_i64, c_int, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_i64]),
+    "randutv_ab_op_name": (ctypes.c_char_p, [c_int]),
+    "randutv_ab_io": (c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_vp,
+                              c_vp]),
     "randutv_profile_enable": (None, [c_int]),
     "randutv_profile_read": (c_int, [c_vp, c_int]),
     "randutv_profile_class_name": (ctypes.c_char_p, [c_int]),
@@ -386,3 +390,52 @@ def randutv_gemm_bf16(transa, alpha, A, B, beta, C, planes=3):
         transa.encode(), M, N, K, alpha, _ptr(A), lda, _ptr(B), ldb, beta, _ptr(C), ldc, planes,
         _stream()))
     return C
+
+
+# ------------------------------------------------------ randUTV by blocks
+
+AB_KINDS = "AGYZBCPQUV"
+
+
+def ab_block_name(blk):
+    """Name of an encoded block: A01, G1, Y0, B1, C1, P0, Q0, U10, V01 (tile indices)."""
+    kind, i, j = blk >> 40, (blk >> 20) & 0xFFFFF, blk & 0xFFFFF
+    letter = AB_KINDS[kind]
+    if letter in "AUV":
+        return f"{letter}{i}{j}" if i < 10 and j < 10 else f"{letter}{i},{j}"
+    return f"{letter}{i}"
+
+
+def ab_tasks(m, n, b, q=0, want_u=False, want_v=False):
+    """The analyzer's task list: [(operation, step, [in blocks], [out blocks])]."""
+    L = lib()
+    count = L.randutv_ab_tasks(m, n, b, q, int(want_u), int(want_v), None, None, None, 0)
+    if count < 0:
+        raise RandutvError("randutv_ab_tasks", int(count))
+    ops = (ctypes.c_int32 * max(count, 1))()
+    steps = (ctypes.c_int32 * max(count, 1))()
+    opnd = (ctypes.c_int64 * max(8 * count, 1))()
+    L.randutv_ab_tasks(m, n, b, q, int(want_u), int(want_v), ops, steps, opnd, count)
+    out = []
+    for t in range(count):
+        ins = [ab_block_name(x) for x in opnd[8 * t:8 * t + 4] if x >= 0]
+        outs = [ab_block_name(x) for x in opnd[8 * t + 4:8 * t + 8] if x >= 0]
+        out.append((L.randutv_ab_op_name(ops[t]).decode(), steps[t], ins, outs))
+    return out
+
+
+def ab_io(m, n, b, q=0, want_u=False, want_v=False, max_tasks=-1, cache_blocks=0, trace=False):
+    """(reads, writes[, trace]) of the traditional (cache_blocks=0) or cached dispatcher."""
+    L = lib()
+    r, w = ctypes.c_int64(0), ctypes.c_int64(0)
+    tr = None
+    if trace and cache_blocks > 0 and max_tasks > 0:
+        tr = (ctypes.c_int64 * (max_tasks * cache_blocks))()
+    _check("randutv_ab_io", L.randutv_ab_io(m, n, b, q, int(want_u), int(want_v), max_tasks,
+                                            cache_blocks, ctypes.byref(r), ctypes.byref(w), tr))
+    if tr is None:
+        return r.value, w.value
+    rows = [[(ab_block_name(x) if x >= 0 else "-") for x in tr[t * cache_blocks:(t + 1) * cache_blocks]]
+            for t in range(max_tasks)]
+    return r.value, w.value, rows
+
