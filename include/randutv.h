@@ -339,6 +339,35 @@ int64_t randutv_ab_tasks(int64_t m, int64_t n, int b, int q, int want_u, int wan
 /* Name of an operation of the task list ("Comp_td_QR", ...). */
 const char* randutv_ab_op_name(int op);
 
+/* randUTV by blocks in HBM (§3.2.2-3.2.3): the analyzer's task list run on
+ * b x b tiles of T (a view of the caller's T), U and V, with every QR done by
+ * blocks (a dense QR of the leading block, triangular-dense QRs below it).
+ * Tasks are spread over `nstreams` (11, 1..16) library streams and ordered by
+ * data flow alone (each waits for the last writer of what it reads and
+ * writes and for the readers of what it writes), with no join between block
+ * steps.  Arguments 1-10 as in randutv_factor_ex (b <= 256); asynchronous on
+ * `stream` (12), device errors from randutv_stream_status().  The result is
+ * the by-blocks factorization: the same method with another orthonormal
+ * completion of each step's Q, so U, T, V differ from randutv_factor beyond
+ * the first block; the first block of U and V spans the same space.
+ * Deterministic: each tile's operations run in task order. */
+int randutv_factor_ab(int64_t m, int64_t n, const double* A, int64_t lda, int b, int q,
+                      uint64_t seed, double* U, double* T, double* V, int nstreams, void* stream);
+
+/* The by-blocks factorization of a matrix in HOST memory (§3.2.4): T (in
+ * place of A, arg 3, lda 4), U (8) and V (9) stay in host memory (pinned for
+ * the copies to overlap) and their b x b blocks pass through an HBM cache of
+ * as many blocks as device_bytes (10) holds beyond the fixed scratch, with
+ * least-recently-used replacement and write-back of modified blocks; loads
+ * and write-backs run on two copy streams beside the compute streams.
+ * device_bytes >= randutv_ooc_ab_min_device_bytes (eight blocks).
+ * io (12, HOST int64[3], optional): blocks read, blocks written, bytes
+ * copied.  Synchronous; returns 0, a device status or -i. */
+size_t randutv_ooc_ab_min_device_bytes(int64_t m, int64_t n, int b, int nstreams);
+int randutv_factor_ooc_ab(int64_t m, int64_t n, double* A, int64_t lda, int b, int q,
+                          uint64_t seed, double* U, double* V, size_t device_bytes, int nstreams,
+                          int64_t* io, void* stream);
+
 /* I/O of the dispatchers of §3.2.4 on the first max_tasks tasks (all when
  * negative) of that list, with every block held in an external store:
  * cache_blocks == 0 is the traditional dispatcher (per task, every input

@@ -14,7 +14,8 @@ _BINDING_NAMES = (
     "randutv_finalize", "randutv_launch_count", "colmajor_empty", "to_colmajor", "lib",
     "RandutvError", "exported_names", "randutv_profile_enable", "randutv_profile_read", "randutv_factor_mixed",
     "randutv_gemm_bf16", "randutv_factor_ooc", "randutv_ooc_min_device_bytes", "randutv_hqrrp",
-    "ab_tasks", "ab_io", "ab_block_name",
+    "ab_tasks", "ab_io", "ab_block_name", "randutv_factor_ab", "randutv_factor_ooc_ab",
+    "randutv_ooc_ab_min_device_bytes",
 )
 
 

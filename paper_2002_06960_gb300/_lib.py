@@ -65,6 +65,11 @@ _SIGS = {
     "randutv_lowrank": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64, c_vp, c_vp]),
     "randutv_lowrank_backward": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_int, c_u64,
                                          c_vp, c_vp, c_vp]),
+    "randutv_factor_ab": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_u64, c_vp, c_vp,
+                                  c_vp, c_int, c_vp]),
+    "randutv_ooc_ab_min_device_bytes": (ctypes.c_size_t, [c_i64, c_i64, c_int, c_int]),
+    "randutv_factor_ooc_ab": (c_int, [c_i64, c_i64, c_vp, c_i64, c_int, c_int, c_u64, c_vp, c_vp,
+                                      ctypes.c_size_t, c_int, c_vp, c_vp]),
     "randutv_ab_tasks": (c_i64, [c_i64, c_i64, c_int, c_int, c_int, c_int, c_vp, c_vp, c_vp, c_i64]),
     "randutv_ab_op_name": (ctypes.c_char_p, [c_int]),
     "randutv_ab_io": (c_int, [c_i64, c_i64, c_int, c_int, c_int, c_int, c_i64, c_i64, c_vp, c_vp,
@@ -438,4 +443,48 @@ def ab_io(m, n, b, q=0, want_u=False, want_v=False, max_tasks=-1, cache_blocks=0
     rows = [[(ab_block_name(x) if x >= 0 else "-") for x in tr[t * cache_blocks:(t + 1) * cache_blocks]]
             for t in range(max_tasks)]
     return r.value, w.value, rows
+
+
+def randutv_factor_ab(A, b, q, seed, want_u=True, want_v=True, nstreams=4):
+    """randUTV by blocks in HBM (tile QRs, tasks ordered by data flow on
+    `nstreams` streams); asynchronous on the current stream.  Returns (U, T, V)."""
+    m, n = A.shape
+    lda = _colmajor(_dev(A, "A"), m, n, "A")
+    T = colmajor_empty(m, n, device=A.device)
+    U = colmajor_empty(m, m, device=A.device) if want_u else None
+    V = colmajor_empty(n, n, device=A.device) if want_v else None
+    _check("randutv_factor_ab", lib().randutv_factor_ab(
+        m, n, _ptr(A), lda, b, q, seed, _ptr(U), _ptr(T), _ptr(V), nstreams, _stream()))
+    return U, T, V
+
+
+def randutv_ooc_ab_min_device_bytes(m, n, b, nstreams=4):
+    return int(lib().randutv_ooc_ab_min_device_bytes(m, n, b, nstreams))
+
+
+def randutv_factor_ooc_ab(A_host, b, q, seed, U_host=None, V_host=None, device_bytes=0,
+                          nstreams=4):
+    """randUTV by blocks with T, U, V in host memory behind an HBM cache of
+    blocks (LRU, write-back of modified blocks).  A_host (CPU float64,
+    column-major, pinned for the copies to overlap) is overwritten by T.
+    device_bytes = 0 takes the minimum plus 64 blocks.  Returns
+    {"reads": blocks read, "writes": blocks written, "bytes": bytes copied}."""
+    m, n = A_host.shape
+    if A_host.is_cuda:
+        raise ValueError("A_host must be a CPU tensor")
+    lda = _colmajor(A_host, m, n, "A_host")
+    for t, r, c, nm in ((U_host, m, m, "U_host"), (V_host, n, n, "V_host")):
+        if t is not None:
+            if t.is_cuda or t.dtype != torch.float64:
+                raise ValueError(f"{nm} must be a CPU float64 tensor")
+            if _colmajor(t, r, c, nm) != r:
+                raise ValueError(f"{nm} must have leading dimension {r}")
+    bb = min(b, m, n)
+    if device_bytes <= 0:
+        device_bytes = randutv_ooc_ab_min_device_bytes(m, n, b, nstreams) + 64 * bb * bb * 8
+    io = (ctypes.c_int64 * 3)()
+    _check("randutv_factor_ooc_ab", lib().randutv_factor_ooc_ab(
+        m, n, _ptr(A_host), lda, b, q, seed, _ptr(U_host), _ptr(V_host), device_bytes, nstreams,
+        io, _stream()))
+    return {"reads": int(io[0]), "writes": int(io[1]), "bytes": int(io[2])}
 

@@ -11,6 +11,9 @@ int launch_philox_normal(uint64_t seed, uint32_t step, uint32_t mid, uint32_t si
                          int64_t cols, double* G, int64_t ldg, cudaStream_t st);
 int launch_philox_normal_f32(uint64_t seed, uint32_t step, uint32_t mid, uint32_t sid,
                              int64_t rows, int64_t cols, float* G, int64_t ldg, cudaStream_t st);
+int launch_philox_normal_rows(uint64_t seed, uint32_t step, uint32_t mid, uint32_t sid,
+                              int64_t rows_total, int64_t row0, int64_t nrows, int64_t cols,
+                              double* G, int64_t ldg, cudaStream_t st);
 int launch_philox_words(uint64_t seed, uint4 c, int64_t count, uint32_t* out, cudaStream_t st);
 
 size_t dgemm_scratch_bytes(int64_t M, int64_t N);

@@ -26,6 +26,41 @@ __global__ void philox_normal_kernel(PhiloxKey key, uint32_t step, uint32_t mid,
   }
 }
 
+// Rows row0 .. row0 + nrows - 1 of the rows_total x cols sketch (element
+// l = r + c rows_total of the whole), into G (nrows x cols, ld ldg): a tile of
+// the sketch that equals the same rows of the whole one.
+__global__ void philox_normal_rows_kernel(PhiloxKey key, uint32_t step, uint32_t mid, uint32_t sid,
+                                          int64_t rows_total, int64_t row0, int64_t nrows,
+                                          int64_t cols, double* __restrict__ G, int64_t ldg) {
+  const int64_t total = nrows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = e % nrows, c = e / nrows;
+    const int64_t l = (row0 + r) + c * rows_total;
+    const uint4 w = philox4x32_10(make_uint4((uint32_t)(l >> 1), step, mid, sid), key);
+    double z0, z1;
+    box_muller(w, &z0, &z1);
+    G[r + c * ldg] = (l & 1) ? z1 : z0;
+  }
+}
+
+int launch_philox_normal_rows(uint64_t seed, uint32_t step, uint32_t mid, uint32_t sid,
+                              int64_t rows_total, int64_t row0, int64_t nrows, int64_t cols,
+                              double* G, int64_t ldg, cudaStream_t st) {
+  const int64_t total = nrows * cols;
+  if (total <= 0) return 0;
+  int64_t blocks = (total + 255) / 256;
+  const int64_t cap = (int64_t)dev_info().sms * 16;
+  if (blocks > cap) blocks = cap;
+  PhiloxKey key{(uint32_t)seed, (uint32_t)(seed >> 32)};
+  ProfScope prof(K_PHILOX, 0.0, 8.0 * (double)total, st);
+  philox_normal_rows_kernel<<<(unsigned)blocks, 256, 0, st>>>(key, step, mid, sid, rows_total,
+                                                              row0, nrows, cols, G, ldg);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
 __global__ void philox_words_kernel(PhiloxKey key, uint4 c, int64_t count, uint32_t* out) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
        i += (int64_t)gridDim.x * blockDim.x) {
