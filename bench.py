@@ -58,6 +58,12 @@ def parse():
                     help="skip the column-pivoted QR (HQRRP) line")
     ap.add_argument("--no-ooc", action="store_true",
                     help="skip the out-of-HBM form (T, U, V in host memory)")
+    ap.add_argument("--no-ab", action="store_true",
+                    help="skip the randUTV-by-blocks lines (in HBM and out of HBM)")
+    ap.add_argument("--no-config2", action="store_true",
+                    help="skip the FP64 sweep over n = 4096, 8192 and q = 0, 1, 2")
+    ap.add_argument("--cpu-sweep", action="store_true",
+                    help="also time the CPU oracle on whole factorizations, n = 512 ... 2048")
     ap.add_argument("--no-backward", action="store_true",
                     help="skip the rank-k backward line (4096^2, k=256, b=128)")
     return ap.parse_args()
@@ -486,6 +492,7 @@ def run_mixed(args, m, n, b, q, steps, warmup, fp64_ms=None):
     track = ((d[:p] / sig.double()) - 1.0).abs()
     del Ad, Ud, Td, Vd, rec
     bg = prof.get("bgemm_tcgen05", {"ms": 0.0, "flops": 0.0})
+    ro = prof.pop("reorth_pass", {"ms": 0.0})
     total_ms = sum(v["ms"] for v in prof.values())
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
@@ -502,6 +509,8 @@ def run_mixed(args, m, n, b, q, steps, warmup, fp64_ms=None):
                    "sigma_track_median_rel_above_1e-3": float(track[res].median())},
         "kernel_shares": {k: round(v["ms"] / total_ms, 4) for k, v in prof.items()
                           if total_ms > 0 and v["launches"]},
+        "reorth_pass": {"ms_per_step": round(ro["ms"] / steps, 2),
+                        "share_of_step": round(ro["ms"] / steps / ms, 4)},
         "roofline": {"bound": "tensor", "kernel": "bgemm_tcgen05 (kind::f16, BF16 MMA flops)",
                      "achieved": round(ach, 2), "peak": bf16_peak, "unit": "TFLOP/s",
                      "frac": round(ach / bf16_peak, 4),
@@ -615,14 +624,145 @@ def run_batched(args, count=4096, lo=64, hi=1024, q=1, steps=3, warmup=3):
                      "frac": round(tf / fp32_peak, 4),
                      "peak_source": "152 SMs x 128 FFMA/clk x 2 flops x 2070 MHz (unit count x max clock)"},
     }
+    # the plain FP64 path on a sample of the same matrices, scaled to the batch by flops
+    import paper_2002_06960_gb300 as pkg
+    sample = torch.randperm(count, generator=gs)[:32].tolist()
+    samp_fl = sum(inputs.algorithmic_flops(*sizes[i], 128, q) for i in sample)
+    mats = [pkg.to_colmajor(As[i].double(), "cuda") for i in sample]
+    pkg.randutv_factor(mats[0], 128, q, 0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for M in mats:
+        pkg.randutv_factor(M, 128, q, 0)
+    torch.cuda.synchronize()
+    samp_s = time.perf_counter() - t0
+    batch_fl64 = sum(inputs.algorithmic_flops(m, n, 128, q) for (m, n) in sizes)
+    est_s = samp_s * batch_fl64 / samp_fl
+    out["fp64_path"] = {"sample": "32 matrices of the batch, one randutv_factor (FP64, b=128) each",
+                        "sample_seconds": round(samp_s, 3),
+                        "estimated_batch_seconds": round(est_s, 2)}
+    out["speedup_vs_fp64_path_estimated"] = round(est_s / (ms * 1e-3), 1)
     plan.close()
-    del As, plan
+    del As, plan, mats
     torch.cuda.empty_cache()
     return out
 
 
 def dev_sms():
     return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+def fp64_factor_ms(A, b=128, q=1, warmup=1, steps=1):
+    """Milliseconds of one plain FP64 randUTV (U, T, V) of the CUDA matrix A."""
+    import paper_2002_06960_gb300 as pkg
+    for _ in range(warmup):
+        pkg.randutv_factor(A, b, q, 0)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        pkg.randutv_factor(A, b, q, 0)
+    e1.record()
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
+# ---------------------------------------------------- randUTV by blocks
+
+def run_ab(args, n=4096, b=256, q=1, nstreams=16, cache_frac=0.25):
+    """randUTV by blocks (§3.2): the analyzer's task list on b x b tiles, in
+    HBM, and with T, U, V in host memory behind an HBM cache of blocks that
+    holds `cache_frac` of their tiles.  Both next to the blocked (fork-join)
+    FP64 path on the same matrix."""
+    import paper_2002_06960_gb300 as pkg
+    A = inputs.gaussian(n, n, 1, device="cuda")
+    Ad = pkg.to_colmajor(A, "cuda")
+    del A
+    flops = inputs.algorithmic_flops(n, n, b, q)
+    pkg.randutv_factor_ab(Ad, b, q, 0, nstreams=nstreams)  # warm-up
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    U, T, V = pkg.randutv_factor_ab(Ad, b, q, 0, nstreams=nstreams)
+    e1.record()
+    e1.synchronize()
+    ms_ab = e0.elapsed_time(e1)
+    if pkg.randutv_stream_status() != 0:
+        raise RuntimeError("randutv_factor_ab failed")
+    g = torch.Generator().manual_seed(0)
+    rows = torch.randperm(n, generator=g)[:64].cuda()
+    recon = float(torch.linalg.norm((U[rows, :] @ T) @ V.T - Ad[rows, :]) /
+                  torch.linalg.norm(Ad[rows, :]))
+    del U, T, V
+    ms_fj = fp64_factor_ms(Ad, b=128, q=q)
+    ms_fj_b = fp64_factor_ms(Ad, b=b, q=q, warmup=0)
+    # out of HBM, cache of cache_frac of the tiles of T, U, V
+    tiles = 3 * ((n + b - 1) // b) ** 2
+    slots = max(8, int(cache_frac * tiles))
+    dev = pkg.randutv_ooc_ab_min_device_bytes(n, n, b, nstreams) + (slots - 8) * b * b * 8
+    Th = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    Uh = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    Vh = pkg.colmajor_empty(n, n, device="cpu", pin=True)
+    Th.copy_(Ad.cpu())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    io = pkg.randutv_factor_ooc_ab(Th, b, q, 0, Uh, Vh, device_bytes=dev, nstreams=nstreams)
+    secs = time.perf_counter() - t0
+    rows_c = rows.cpu()
+    rec_o = float(torch.linalg.norm((Uh[rows_c, :] @ Th) @ Vh.T - Ad.cpu()[rows_c, :]) /
+                  torch.linalg.norm(Ad.cpu()[rows_c, :]))
+    tasks = pkg.ab_tasks(n, n, b, q=q, want_u=True, want_v=True)
+    trad_r = sum(sum(1 for x in ins if x[0] in "AUV") for _, _, ins, _ in tasks)
+    trad_w = sum(sum(1 for x in outs if x[0] in "AUV") for _, _, _, outs in tasks)
+    out = {
+        "workload": f"randutv_ab_fp64_n{n}_b{b}_q{q}",
+        "value": round(flops / (ms_ab * 1e-3) / 1e12, 4), "unit": "TFLOP/s",
+        "ms": round(ms_ab, 1), "streams": nstreams, "tasks": len(tasks),
+        "fork_join_ms_b128": round(ms_fj, 1), f"fork_join_ms_b{b}": round(ms_fj_b, 1),
+        "time_vs_fork_join_b128": round(ms_ab / ms_fj, 3),
+        "errors": {"recon_sampled_rows": recon},
+        "out_of_hbm": {
+            "seconds": round(secs, 3), "value": round(flops / secs / 1e12, 4), "unit": "TFLOP/s",
+            "cache_blocks": slots, "blocks_of_T_U_V": tiles,
+            "blocks_read": io["reads"], "blocks_written": io["writes"],
+            "bytes_copied": io["bytes"],
+            "traditional_dispatcher_blocks_read_written": [trad_r, trad_w],
+            "recon_sampled_rows": rec_o,
+        },
+    }
+    del Ad, Th, Uh, Vh
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_config2(args):
+    """Plain FP64 randUTV at n = 4096 and 8192 for q = 0, 1, 2 (b = 128), i.i.d.
+    N(0,1) input: seconds, algorithmic TFLOP/s, t / n^3 * 1e10, sampled errors."""
+    import paper_2002_06960_gb300 as pkg
+    rows_out = []
+    for n in (4096, 8192):
+        A = pkg.to_colmajor(inputs.gaussian(n, n, 1, device="cuda"), "cuda")
+        pkg.randutv_factor(A, 128, 0, 0)  # warm-up at this size
+        for q in (0, 1, 2):
+            ms = fp64_factor_ms(A, 128, q, warmup=0)
+            U, T, V = pkg.randutv_factor(A, 128, q, 0)
+            g = torch.Generator().manual_seed(0)
+            rows = torch.randperm(n, generator=g)[:64].cuda()
+            recon = float(torch.linalg.norm((U[rows, :] @ T) @ V.T - A[rows, :]) /
+                          torch.linalg.norm(A[rows, :]))
+            fl = inputs.algorithmic_flops(n, n, 128, q)
+            rows_out.append({"n": n, "q": q, "seconds": round(ms / 1e3, 3),
+                             "tflops": round(fl / (ms * 1e-3) / 1e12, 4),
+                             "t_over_n3_e10": round(ms / 1e3 / n ** 3 * 1e10, 5),
+                             "recon_sampled_rows": recon})
+            del U, T, V
+        del A
+        torch.cuda.empty_cache()
+    return rows_out
+
+
+def fp64_factor_ms_of(A, b, q):
+    return fp64_factor_ms(A, b, q)
 
 
 def run_backward(args, n=4096, k=256, b=128, q=1, steps=3, warmup=2, fp64_factor_ms=None):
@@ -685,8 +825,11 @@ def run_backward(args, n=4096, k=256, b=128, q=1, steps=3, warmup=2, fp64_factor
         "input": "Q1 diag(step at k: 1 then 1e-6) Q2^T, B i.i.d. N(0,1)",
         "gradient_rel_error_vs_central_differences": [float(f"{e:.3e}") for e in errs],
     }
-    if fp64_factor_ms:
-        out["ratio_to_fp64_full_factorization_same_n"] = round(ms_fb / fp64_factor_ms, 4)
+    import paper_2002_06960_gb300 as pkg
+    if not fp64_factor_ms:
+        fp64_factor_ms = fp64_factor_ms_of(pkg.to_colmajor(A, "cuda"), b, q)
+    out["fp64_full_factorization_ms_same_n"] = round(fp64_factor_ms, 1)
+    out["speedup_vs_fp64_path_same_n"] = round(fp64_factor_ms / ms_fb, 3)
     del A, B, grad, R
     torch.cuda.empty_cache()
     return out
@@ -708,6 +851,32 @@ def oracle_sample(n, b, q, seed, steps, A=None):
             "cores": torch.get_num_threads(), "kind": "oracle",
             "sample": f"first {steps} block step(s) of the {n}x{n} b={b} q={q} FP64 "
                       f"factorization with U and V ({flops:.3e} algorithmic flops, {dt:.1f} s)"}
+
+
+def cpu_sweep(args, sizes=(512, 1024, 2048), b=128, q=1):
+    """The CPU oracle on whole factorizations (U, T, V), i.i.d. N(0,1), median
+    of 3 (1 at 2048); larger n extrapolated by t / n^3 and labelled so."""
+    import oracle
+    rows = []
+    for n in sizes:
+        A = inputs.gaussian(n, n, 1)
+        reps = 3 if n < 2048 else 1
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            oracle.randutv(A, b, q, 0)
+            ts.append(time.perf_counter() - t0)
+        t = statistics.median(ts)
+        fl = inputs.algorithmic_flops(n, n, b, q)
+        rows.append({"n": n, "seconds": round(t, 3), "tflops": round(fl / t / 1e12, 4),
+                     "t_over_n3_e10": round(t / n ** 3 * 1e10, 4), "measured": True})
+    c = rows[-1]["t_over_n3_e10"]
+    for n in (4096, 8192, 16384):
+        t = c * n ** 3 / 1e10
+        rows.append({"n": n, "seconds": round(t, 1),
+                     "tflops": round(inputs.algorithmic_flops(n, n, b, q) / t / 1e12, 4),
+                     "measured": False, "extrapolated_from_n": sizes[-1]})
+    return {"cores": torch.get_num_threads(), "b": b, "q": q, "rows": rows}
 
 
 def _flops_first_steps(n, b, q, steps):
@@ -778,6 +947,21 @@ def main():
                 args, fp64_factor_ms=out["ms_per_step"] if args.n == 4096 else None)
         except Exception as e:  # report, never hide
             out["backward"] = {"error": repr(e)}
+    if world == 1 and not args.no_ab:
+        try:
+            out["by_blocks"] = run_ab(args)
+        except Exception as e:  # report, never hide
+            out["by_blocks"] = {"error": repr(e)}
+    if world == 1 and not args.no_config2:
+        try:
+            out["fp64_sweep"] = run_config2(args)
+        except Exception as e:  # report, never hide
+            out["fp64_sweep"] = {"error": repr(e)}
+    if rank == 0 and world == 1 and args.cpu_sweep:
+        try:
+            out["cpu_sweep"] = cpu_sweep(args)
+        except Exception as e:  # report, never hide
+            out["cpu_sweep"] = {"error": repr(e)}
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = oracle_sample(args.n, args.b, args.q, args.seed,

@@ -372,6 +372,7 @@ int mixed_flush_folds(MCtx& c) {
 int mixed_reorth(MCtx& c, float* To, float* Uo, float* Vo) {
   MixedWork& w = c.w;
   const int64_t m = c.m, n = c.n, p = m < n ? m : n;
+  ProfScope prof(K_REORTH, 0.0, 0.0, c.st);
   if (c.want_u) {
     Planes P = w.Ut;  // m x m, now the planes of U (not U^T)
     RUTV_TRY(split_f32(Uo, m, m, m, 0, P, 0, 0, c.st));
