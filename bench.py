@@ -555,17 +555,9 @@ def run_batched(args, count=4096, lo=64, hi=1024, q=1, steps=3, warmup=3):
         As.append(A)
     haar.clear()
 
-    def make(m, n, i):
-        gg = torch.Generator(device="cuda")
-        gg.manual_seed(1000 + i)
-        p = min(m, n)
-        sig = torch.exp(-torch.arange(p, dtype=torch.float64, device="cuda") / 16.0)
-        A = pkg.colmajor_empty(m, n, device="cuda", dtype=torch.float32)
-        A.copy_((_haar_gpu(m, p, gg) * sig) @ _haar_gpu(n, p, gg).T)
-        return A
-
     t0 = time.time()
-    tune = batched.autotune(make, per_class=24, q=q)
+    tuned = batched.autotune_batch(As, q=q)
+    tune = tuned["b"]
     tune_s = time.time() - t0
     plan = batched.BatchedPlan(As, b=0, q=q, seed=0)
     stream = torch.cuda.Stream()
@@ -616,6 +608,9 @@ def run_batched(args, count=4096, lo=64, hi=1024, q=1, steps=3, warmup=3):
         "input": "Q1 diag(exp(-j/16)) Q2^T per matrix, FP32; sizes seeded (stream 5)",
         "launch": "one persistent kernel per step, replayed from a CUDA graph",
         "autotune": {str(c): {"b": v[0], "ms": round(v[1], 3)} for c, v in tune.items()},
+        "autotune_ctas_per_sm": {"choice": tuned["ctas_per_sm"][0],
+                                 "ms": round(tuned["ctas_per_sm"][1], 2),
+                                 "note": "0 = occupancy limit; tuned on the batch itself"},
         "autotune_seconds": round(tune_s, 1),
         "failed_matrices": bad,
         "errors_worst_of_16": worst,

@@ -5,7 +5,11 @@ host pointer arrays of ``randutv_batched_plan_create``; ``run()`` is one
 memset and one persistent kernel launch on the current stream, so it can be
 captured in a CUDA graph.  ``autotune()`` times the launch for each block
 size allowed (16, 32, 64) on seeded matrices of every size class and hands
-the fastest to the library.
+the fastest to the library; ``autotune_batch()`` does the same on the
+matrices of the batch it will serve, at full occupancy (up to two CTAs per
+SM of matrices per class), and then picks the CTAs per SM of the grid.
+The CTA tile of the products is not a tuning knob: the kernel takes 64 x 64
+tiles, or 128 x 32 / 32 x 128 when one side of the output is at most 32.
 """
 from __future__ import annotations
 
@@ -120,3 +124,52 @@ def autotune(make_matrix, per_class=24, q=1, reps=2, classes=None):
         report[c] = best
     set_tuning(table)
     return report
+
+
+def _time_plan(mats, b, q, reps):
+    plan = BatchedPlan(mats, b=b, q=q, seed=0)
+    plan.run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        plan.run()
+    e1.record()
+    e1.synchronize()
+    plan.close()
+    return e0.elapsed_time(e1) / reps
+
+
+def autotune_batch(mats, q=1, reps=2, per_class=None, ctas_choices=(0, 1)):
+    """Tune on the batch itself.  For each size class, time its first
+    ``per_class`` matrices (default: two per SM, so the launch is as full as
+    in the real run) with every b in B_CHOICES and keep the fastest; then time
+    the whole batch with the resulting table for each CTAs-per-SM choice (0 =
+    the occupancy limit) and keep the fastest.  Installs the table and
+    returns {"b": {class: (b, ms)}, "ctas_per_sm": (choice, ms)}."""
+    if per_class is None:
+        per_class = 2 * torch.cuda.get_device_properties(mats[0].device).multi_processor_count
+    groups = {}
+    for A in mats:
+        groups.setdefault(size_class(A.shape[0], A.shape[1]), []).append(A)
+    table = [0] * N_CLASSES
+    report = {}
+    set_tuning(table, 0)
+    for c in sorted(groups):
+        sample = groups[c][:per_class]
+        best = None
+        for b in B_CHOICES:
+            ms = _time_plan(sample, b, q, reps)
+            if best is None or ms < best[1]:
+                best = (b, ms)
+        table[c] = best[0]
+        report[c] = best
+    best_c = None
+    for cps in ctas_choices:
+        set_tuning(table, cps)
+        ms = _time_plan(mats, 0, q, reps)
+        if best_c is None or ms < best_c[1]:
+            best_c = (cps, ms)
+    set_tuning(table, best_c[0])
+    return {"b": report, "ctas_per_sm": best_c}
+

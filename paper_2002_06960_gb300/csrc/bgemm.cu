@@ -14,11 +14,13 @@
 //   A is K-major when op(A) = X^T (A(m, k) = X[k + m ldx]) and MN-major when
 //   op(A) = X (A(m, k) = X[m + k ldx]); both are BF16 (kind::f16), for which
 //   the MMA takes either major-ness.
-// Tile 128 x 128 x 64, cta_group::1, accumulator 128 lanes x 128 FP32
-// columns of tensor memory.  Warp 0 issues TMA loads (and owns the TMEM
+// Tile 128 x 64 x 64 (BM x BN x BK), cta_group::1; tensor memory holds two
+// accumulator buffers of 128 lanes x 2 BN FP32 columns (the leading product
+// and the correction products of the split).  Warp 0 issues TMA loads (and owns the TMEM
 // allocation), warp 1 issues the MMAs, warps 2-5 drain the accumulator.
 // Every mbarrier wait is bounded; on timeout the kernel records
 // RANDUTV_ETIMEOUT, lets its copies in flight land, frees TMEM and returns.
+#include <algorithm>
 #include <cstring>
 
 #include <cuda.h>
@@ -27,6 +29,7 @@
 
 #include "common.cuh"
 #include "mixed.h"
+#include "tcgen05.cuh"
 
 namespace rutv {
 
@@ -42,49 +45,6 @@ constexpr int C_TILE = C_ELEMS * 2;  // its bytes
 constexpr int C_ROWS = 32;           // rows of one epilogue warp's slice (box C_ROWS x BN)
 constexpr int C_SLICE = C_ROWS * BN; // elements of a slice, column-major (ld C_ROWS)
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-      " selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on the phase with the given parity; false (and err set) on timeout.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned* err,
-                                          unsigned site) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = globaltimer_ns();
-  unsigned spins = 0;
-  while (!mbar_try_wait(bar, parity)) {
-    if ((++spins & 255u) == 0) {
-      if (*(volatile unsigned*)err != 0) return false;
-      if (globaltimer_ns() - t0 > kWaitLimitNs) {
-        if (atomicCAS(err, 0u, (unsigned)RANDUTV_ETIMEOUT) == 0u) atomicExch(err + 1, site);
-        return false;
-      }
-    }
-  }
-  return true;
-}
-
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
   asm volatile(
@@ -92,18 +52,6 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, u
       " [%0], [%1, {%3, %4}], [%2];" ::"r"(smem_u32(dst)),
       "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
       : "memory");
-}
-
-// Shared-memory matrix descriptor (sm_100 format): start address, leading
-// and stride byte offsets (all >> 4), version 1, 128-byte swizzle.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version for sm_100
-  d |= (uint64_t)2 << 61;  // SWIZZLE_128B
-  return d;
 }
 
 // Instruction descriptor, kind::f16: BF16 x BF16 -> FP32, M = 128, N = 128.
@@ -117,40 +65,6 @@ __device__ __forceinline__ uint32_t instr_desc(int a_mn_major) {
   d |= (uint32_t)(BN >> 3) << 17;  // N / 8
   d |= (uint32_t)(BM >> 4) << 24;  // M / 16
   return d;
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t idesc, uint32_t accumulate) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-      : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_u32(bar))
-      : "memory");
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, "
-      "%28, %29, %30, %31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // TMA store of a 2-D box from shared memory (bulk-group completion).
@@ -168,15 +82,6 @@ __device__ __forceinline__ void bulk_wait_read() {
 }
 // wait until the committed bulk stores are complete
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
-// generic-proxy writes to shared memory made visible to the async (TMA) proxy
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
 // Error-free transformation of a sum: s + e == a + b exactly (Knuth's two-sum).
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
@@ -196,6 +101,11 @@ struct BgemmParams {
   int a_x0, a_y0;      // coordinate offsets of A's source (x = source row, y = source col)
   int b_x0, b_y0;
   int stages;
+  int drain_per_tile;  // one-plane products: accumulate the whole K in TMEM, drain once
+  int out_upper;       // skip tiles wholly below the diagonal (their C is not wanted)
+  int a_upper;         // op(A) upper triangular: K from the tile's first row
+  int b_upper;         // B(k, n) = 0 for k > n: K up to the tile's last column
+  int b_lower;         // B(k, n) = 0 for k < n: K from the tile's first column
   int mode;            // 0: C = alpha acc + beta C (FP32); 1: planes += alpha acc
   float alpha, beta;
   float* C;            // mode 0
@@ -206,6 +116,22 @@ struct BgemmParams {
   int64_t ldp;
   unsigned* err;
 };
+
+// Output tile `tile` of the persistent order: its corner and its K steps
+// [kb, ke); false when the tile is skipped (wholly below the diagonal with
+// out_upper, or no K step that can contribute).
+__device__ __forceinline__ bool tile_range(const BgemmParams& p, int tile, int& m0, int& n0,
+                                           int& kb, int& ke) {
+  m0 = (tile / p.tiles_n) * BM;
+  n0 = (tile % p.tiles_n) * BN;
+  if (p.out_upper && m0 >= n0 + BN) return false;
+  kb = 0;
+  ke = p.ksteps;
+  if (p.a_upper) kb = max(kb, m0 / BK);
+  if (p.b_lower) kb = max(kb, n0 / BK);
+  if (p.b_upper) ke = min(ke, (n0 + BN + BK - 1) / BK);
+  return kb < ke;
+}
 
 // Persistent over output tiles (tile t -> rows (t / tiles_n) BM, columns
 // (t % tiles_n) BN).  The tensor-memory accumulator is drained every K step
@@ -235,7 +161,6 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
   uint32_t* tmem_slot = (uint32_t*)(cfree + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ksteps = p.ksteps;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < p.stages; ++s) {
@@ -270,8 +195,9 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
       int cl = 0;  // output-plane loads issued
       bool run = true;
       for (int tile = blockIdx.x; run && tile < p.ntiles; tile += gridDim.x) {
-        const int m0 = (tile / p.tiles_n) * BM, n0 = (tile % p.tiles_n) * BN;
-        for (int ks = 0; ks < ksteps; ++ks, ++g) {
+        int m0, n0, kb, ke;
+        if (!tile_range(p, tile, m0, n0, kb, ke)) continue;
+        for (int ks = kb; ks < ke; ++ks, ++g) {
           const int s = g % p.stages;
           const int round = g / p.stages;
           if (round > 0 && !mbar_wait(&empty[s], (uint32_t)((round - 1) & 1), p.err, 11)) {
@@ -322,8 +248,45 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
       const uint32_t idesc = instr_desc(p.a_mn);
       int g = 0;
       bool run = true;
+      int tl = 0;  // tiles of this CTA
       for (int tile = blockIdx.x; run && tile < p.ntiles; tile += gridDim.x) {
-        for (int ks = 0; ks < ksteps; ++ks, ++g) {
+        int m0, n0, kb, ke;
+        if (!tile_range(p, tile, m0, n0, kb, ke)) continue;
+        if (p.drain_per_tile) {
+          // one accumulator per tile over all of K, in TMEM buffer tl & 1
+          const int buf = tl & 1, use = tl >> 1;
+          if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), p.err, 16)) {
+            run = false;
+            break;
+          }
+          uint32_t accum = 0u;
+          for (int ks = kb; ks < ke; ++ks, ++g) {
+            const int s = g % p.stages;
+            if (!mbar_wait(&full[s], (uint32_t)((g / p.stages) & 1), p.err, 13)) {
+              run = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = smem_u32(smem + (size_t)s * per_stage);
+            const uint32_t b_addr = st + p.na * A_TILE;
+#pragma unroll
+            for (int kk = 0; kk < BK / 16; ++kk) {
+              uint64_t ad;
+              if (p.a_mn) ad = smem_desc(st + kk * 2048, A_TILE / 2, 1024);
+              else        ad = smem_desc(st + kk * 32, 16, 1024);
+              const uint64_t bd = smem_desc(b_addr + kk * 32, 16, 1024);
+              mma_bf16(tmem + (uint32_t)(buf * 2 * BN), ad, bd, idesc, accum);
+              accum = 1u;
+            }
+            mma_commit(&empty[s]);
+          }
+          if (!run) break;
+          mma_commit(&acc_full[buf]);
+          ++tl;
+          continue;
+        }
+        ++tl;
+        for (int ks = kb; ks < ke; ++ks, ++g) {
           const int buf = g & 1, use = g >> 1;
           if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), p.err, 16)) {
             run = false;
@@ -368,11 +331,24 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     int tl = 0;  // tiles of this CTA
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
-      const int m0 = (tile / p.tiles_n) * BM, n0 = (tile % p.tiles_n) * BN;
+      int m0, n0, kb, ke;
+      if (!tile_range(p, tile, m0, n0, kb, ke)) continue;
       float sum[BN], cmp[BN];
 #pragma unroll
       for (int i = 0; i < BN; ++i) { sum[i] = 0.f; cmp[i] = 0.f; }
-      for (int ks = 0; ks < ksteps; ++ks, ++g) {
+      if (p.drain_per_tile) {
+        const int buf = tl & 1, use = tl >> 1;
+        bool w = mbar_wait(&acc_full[buf], (uint32_t)(use & 1), p.err, 14);
+        ok = __all_sync(0xffffffffu, w) && ok;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int cc = 0; cc < BN; cc += 32) tmem_ld32(tmem + lane_base + (uint32_t)(buf * 2 * BN + cc), sum + cc);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+      }
+      for (int ks = kb; !p.drain_per_tile && ks < ke; ++ks, ++g) {
         const int buf = g & 1, use = g >> 1;
         bool w = mbar_wait(&acc_full[buf], (uint32_t)(use & 1), p.err, 14);
         ok = __all_sync(0xffffffffu, w) && ok;
@@ -531,9 +507,12 @@ int make_tmap_bf16(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, in
 }
 
 int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int K, int pairs_mode,
-                 const BgemmOut& out, unsigned* err, cudaStream_t st, int max_ctas) {
+                 const BgemmOut& out, unsigned* err, cudaStream_t st, int max_ctas,
+                 const BgemmTri& tri) {
   if (M <= 0 || N <= 0) return 0;
   if (K <= 0) return RANDUTV_EUNSUPPORTED;  // no product to accumulate
+  if ((tri.a_upper || tri.b_upper || tri.b_lower) && !(out.mode == 0 && out.beta == 1.f))
+    return RANDUTV_EUNSUPPORTED;  // skipped K ranges leave C as it is
   BgemmParams p;
   memset(&p, 0, sizeof p);
   p.na = A.nplanes;
@@ -590,13 +569,35 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.tiles_n = (N + BN - 1) / BN;
   p.ntiles = tiles_m * p.tiles_n;
   p.ksteps = (K + BK - 1) / BK;
+  p.drain_per_tile = (p.npairs == 1) ? 1 : 0;
+  p.out_upper = tri.out_upper;
+  p.a_upper = tri.a_upper;
+  p.b_upper = tri.b_upper;
+  p.b_lower = tri.b_lower;
+  // MMA flops of the tiles and K steps that run (for tracing)
+  double mma_flops = 2.0 * M * (double)N * K * p.npairs;
+  if (tri.out_upper || tri.a_upper || tri.b_upper || tri.b_lower) {
+    mma_flops = 0.0;
+    for (int t = 0; t < tiles_m * p.tiles_n; ++t) {
+      const int m0 = (t / p.tiles_n) * BM, n0 = (t % p.tiles_n) * BN;
+      if (tri.out_upper && m0 >= n0 + BN) continue;
+      int kb = 0, ke = p.ksteps;
+      if (tri.a_upper) kb = std::max(kb, m0 / BK);
+      if (tri.b_lower) kb = std::max(kb, n0 / BK);
+      if (tri.b_upper) ke = std::min(ke, (n0 + BN + BK - 1) / BK);
+      if (kb >= ke) continue;
+      const double rows = std::min(BM, M - m0), cols = std::min(BN, N - n0);
+      const double kk = std::min(ke * BK, K) - kb * BK;
+      mma_flops += 2.0 * rows * cols * kk * p.npairs;
+    }
+  }
   const size_t smem = 1024 + (size_t)stages * per_stage + ctile_bytes + (2 * stages + 7) * 8 + 16;
   RUTV_TRY(ensure_smem((const void*)bgemm_kernel, smem));
   // persistent: at most one CTA per SM (the shared memory allows no more)
   int cap = dev_info().sms;
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
   const int grid = p.ntiles < cap ? p.ntiles : cap;
-  ProfScope prof(K_BGEMM, 2.0 * M * (double)N * K * p.npairs,
+  ProfScope prof(K_BGEMM, mma_flops,
                  2.0 * ((double)M * K * p.na + (double)K * N * p.nb) +
                      (out.mode == 0 ? 4.0 : 12.0) * M * (double)N,
                  st);

@@ -35,7 +35,7 @@ void note_launch(int n = 1);
 // library is bracketed by a CUDA event pair on its stream and tagged with the
 // algorithmic flops and bytes of that launch.
 enum KernelClass { K_PHILOX = 0, K_DGEMM, K_QR, K_WY, K_SVD, K_OTHER, K_BGEMM, K_CONVERT,
-                   K_SVD32, K_REORTH, K_NCLASS };  // K_REORTH spans a whole pass (its
+                   K_SVD32, K_REORTH, K_ADJOINT, K_NCLASS };  // K_REORTH spans a whole pass (its
                                                   // launches also count in their own class)
 struct ProfScope {
   ProfScope(int cls, double flops, double bytes, cudaStream_t st);

@@ -87,21 +87,22 @@ __global__ void hqr_rev_rows(int r, int c, int j, double tau, double vv, double*
 
 // K3: reverse of the generation of reflector j from its column x (rows j..r-1).
 // One block.  Restores X(j:, j) = x and writes its adjoint into Xb(j:, j).
-__global__ void hqr_rev_gen(int r, int c, int j, double tau, double* __restrict__ X,
+// vv = v.v (the host holds W and computes it once per column).
+__global__ void hqr_rev_gen(int r, int c, int j, double tau, double vv, double* __restrict__ X,
                             double* __restrict__ Xb, const double* __restrict__ W,
                             const double* __restrict__ Wb, double taub_in,
                             const double* __restrict__ ap) {
   __shared__ double red[32];
   __shared__ double sh[4];
   const double beta = X[j + (int64_t)j * r];
-  // tau adjoint from the trailing update: -sum_l p_l s_l
-  double tb = 0.0;
-  if (threadIdx.x == 0) {
-    double vv = 0.0;
-    for (int i = j; i < r; ++i) vv = fma(W[i + (int64_t)j * r], W[i + (int64_t)j * r], vv);
+  // tau adjoint from the trailing update: -sum_l p_l s_l, summed by the first
+  // warp in a fixed order (lanes stride the columns, then a shuffle tree)
+  if (threadIdx.x < 32) {
     const double sfac = 1.0 - tau * vv;
-    for (int l = j + 1; l < c; ++l) tb -= ap[2 * l + 1] * ap[2 * l] * sfac;
-    sh[0] = tb + taub_in;
+    double tb = 0.0;
+    for (int l = j + 1 + (int)threadIdx.x; l < c; l += 32) tb -= ap[2 * l + 1] * ap[2 * l] * sfac;
+    for (int o = 16; o > 0; o >>= 1) tb += __shfl_xor_sync(0xffffffffu, tb, o);
+    if (threadIdx.x == 0) sh[0] = tb + taub_in;
   }
   __syncthreads();
   const double taub = sh[0];
@@ -280,6 +281,7 @@ int hqr_reverse(LCtx& c, int64_t r, int64_t b, double* X, const double* W, const
   RUTV_CK(cudaMemcpyAsync(Wh.data(), W, (size_t)r * b * 8, cudaMemcpyDeviceToHost, c.st));
   RUTV_CK(cudaStreamSynchronize(c.st));
   RUTV_TRY(zero(c, Pb, (size_t)r * b));
+  ProfScope prof(K_ADJOINT, 4.0 * (double)r * b * b, 40.0 * (double)r * b, c.st);
   for (int64_t j = b - 1; j >= 0; --j) {
     double vv = 0.0;
     for (int64_t i = j; i < r; ++i) vv += Wh[i + j * r] * Wh[i + j * r];
@@ -290,7 +292,8 @@ int hqr_reverse(LCtx& c, int64_t r, int64_t b, double* X, const double* W, const
                                                                       tau[j], vv, X, Pb, W, Wb, ap);
       note_launch(2);
     }
-    hqr_rev_gen<<<1, 512, 0, c.st>>>((int)r, (int)b, (int)j, tau[j], X, Pb, W, Wb, taub[j], ap);
+    hqr_rev_gen<<<1, 512, 0, c.st>>>((int)r, (int)b, (int)j, tau[j], vv, X, Pb, W, Wb, taub[j],
+                                     ap);
     note_launch();
     RUTV_CK(cudaGetLastError());
   }
@@ -338,7 +341,10 @@ int left_apply_rev(LCtx& c, int64_t rows, int64_t cols, int64_t b, const double*
 int larft_reverse(LCtx& c, int64_t r, int64_t b, const double* W, const double* tau,
                   const double* S, const double* Gm, double* Sb, double* Wb, double* taub,
                   double* Gb) {
-  larft_rev_kernel<<<1, 256, 0, c.st>>>((int)b, S, Gm, tau, Sb, Gb, taub);
+  {
+    ProfScope prof(K_ADJOINT, (double)b * b * b, 32.0 * (double)b * b, c.st);
+    larft_rev_kernel<<<1, 256, 0, c.st>>>((int)b, S, Gm, tau, Sb, Gb, taub);
+  }
   note_launch();
   RUTV_CK(cudaGetLastError());
   RUTV_TRY(G(c, false, false, r, b, b, 1.0, W, r, Gb, b, 1.0, Wb, r));

@@ -376,28 +376,40 @@ int mixed_reorth(MCtx& c, float* To, float* Uo, float* Vo) {
   if (c.want_u) {
     Planes P = w.Ut;  // m x m, now the planes of U (not U^T)
     RUTV_TRY(split_f32(Uo, m, m, m, 0, P, 0, 0, c.st));
+    BgemmTri upper_only;  // only E's tiles on and above the diagonal are read
+    upper_only.out_upper = 1;
     RUTV_TRY(launch_bgemm(opnd(P, 3, 0, 0, 0), opnd(P, 3, 0, 0, 0), (int)m, (int)m, (int)m, 3,
-                          out_f32(w.E, m), c.status, c.st));
+                          out_f32(w.E, m), c.status, c.st, 0, upper_only));
     RUTV_TRY(reorth_phi(Uo, m, m, w.E, m, w.dcol, w.Phi, pad8(m), nullptr, 0, c.st));
     // U -= U Phi_U
+    BgemmTri tri;
+    tri.b_upper = 1;  // Phi_U upper triangular
     RUTV_TRY(launch_bgemm(opnd(P, 1, 0, 0, 1), opnd_bf16(w.Phi, m, m, pad8(m), 0), (int)m, (int)m,
-                          (int)m, 1, out_f32(Uo, m, -1.f, 1.f), c.status, c.st));
+                          (int)m, 1, out_f32(Uo, m, -1.f, 1.f), c.status, c.st, 0, tri));
     // T += Phi_U T
+    tri.a_upper = 1;  // Phi_U and T both upper triangular
     RUTV_TRY(launch_bgemm(opnd_bf16(w.Phi, m, m, pad8(m), 1), opnd(w.T, 1, 0, 0, 0), (int)m,
-                          (int)n, (int)m, 1, out_f32(To, m, 1.f, 1.f), c.status, c.st));
+                          (int)n, (int)m, 1, out_f32(To, m, 1.f, 1.f), c.status, c.st, 0, tri));
   }
   if (c.want_v) {
     Planes P = w.Vt;  // n x n, now the planes of V
     RUTV_TRY(split_f32(Vo, n, n, n, 0, P, 0, 0, c.st));
+    BgemmTri upper_only;
+    upper_only.out_upper = 1;
     RUTV_TRY(launch_bgemm(opnd(P, 3, 0, 0, 0), opnd(P, 3, 0, 0, 0), (int)n, (int)n, (int)n, 3,
-                          out_f32(w.E, n), c.status, c.st));
+                          out_f32(w.E, n), c.status, c.st, 0, upper_only));
     RUTV_TRY(reorth_phi(Vo, n, n, w.E, n, w.dcol, w.Phi, pad8(n), w.PhiT, pad8(n), c.st));
     // V -= V Phi_V^T
+    BgemmTri lower;
+    lower.b_lower = 1;  // Phi_V^T lower triangular
     RUTV_TRY(launch_bgemm(opnd(P, 1, 0, 0, 1), opnd_bf16(w.PhiT, n, n, pad8(n), 0), (int)n, (int)n,
-                          (int)n, 1, out_f32(Vo, n, -1.f, 1.f), c.status, c.st));
+                          (int)n, 1, out_f32(Vo, n, -1.f, 1.f), c.status, c.st, 0, lower));
     // T += T Phi_V
+    BgemmTri tri;
+    tri.a_upper = 1;  // T and Phi_V both upper triangular
+    tri.b_upper = 1;
     RUTV_TRY(launch_bgemm(opnd(w.T, 1, 0, 0, 1), opnd_bf16(w.Phi, n, n, pad8(n), 0), (int)m,
-                          (int)n, (int)n, 1, out_f32(To, m, 1.f, 1.f), c.status, c.st));
+                          (int)n, (int)n, 1, out_f32(To, m, 1.f, 1.f), c.status, c.st, 0, tri));
   }
   if (c.want_u || c.want_v) RUTV_TRY(zero_block_offdiag(To, m, p, c.b, c.st));
   return 0;

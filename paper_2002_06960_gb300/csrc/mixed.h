@@ -43,12 +43,24 @@ struct BgemmOut {
   int64_t ldp = 0;
 };
 
-// pairs_mode 1: one BF16 product of plane 0 of A and B.  pairs_mode 3: the
-// six products A_i B_j with i + j <= 2 of three planes each (FP32 accuracy).
+// Structure of the operands that lets tiles or K steps be skipped:
+//   out_upper: only output tiles that reach the diagonal or above are wanted;
+//   a_upper:   op(A) is upper triangular;
+//   b_upper:   B(k, n) = 0 for k > n;  b_lower: B(k, n) = 0 for k < n.
+// With a_upper, b_upper or b_lower a tile whose K range is empty is left as
+// it is, which is the product only for mode 0 with beta = 1 (required).
+struct BgemmTri {
+  int out_upper = 0, a_upper = 0, b_upper = 0, b_lower = 0;
+};
+
+// pairs_mode 1: one BF16 product of plane 0 of A and B (accumulated over the
+// whole K in tensor memory).  pairs_mode 3: the six products A_i B_j with
+// i + j <= 2 of three planes each (FP32 accuracy; the accumulator is
+// drained every 64 K into compensated sums).
 // max_ctas: upper bound on the persistent grid (0 = one CTA per SM).
 int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int K,
                  int pairs_mode, const BgemmOut& out, unsigned* err, cudaStream_t st,
-                 int max_ctas = 0);
+                 int max_ctas = 0, const BgemmTri& tri = BgemmTri());
 
 int make_tmap_bf16(CUtensorMap* map, const __nv_bfloat16* base, int64_t rows, int64_t cols,
                    int64_t ld, int box_cols);

@@ -582,7 +582,8 @@ int randutv_profile_read(double* out, int nclass) {
 const char* randutv_profile_class_name(int cls) {
   static const char* names[K_NCLASS] = {"philox_normal", "dgemm", "householder_panel",
                                         "wy_factor", "jacobi_svd", "other", "bgemm_tcgen05",
-                                        "convert", "jacobi_svd_fp32", "reorth_pass"};
+                                        "convert", "jacobi_svd_fp32", "reorth_pass",
+                                        "qr_adjoint"};
   return (cls >= 0 && cls < K_NCLASS) ? names[cls] : "?";
 }
 

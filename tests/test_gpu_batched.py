@@ -127,6 +127,22 @@ def test_autotuner_installs_a_table(pkg):
     batched.set_tuning([0] * batched.N_CLASSES)  # back to the default
 
 
+def test_batch_autotuner_tunes_on_the_batch(pkg):
+    p, batched = pkg
+    mats = [d for _, d in _mats(p, [(100, 90), (90, 120), (300, 250), (260, 300), (40, 40)] * 4,
+                                 seed=21)]
+    rep = batched.autotune_batch(mats, q=1, reps=1)
+    assert set(rep["b"]) == {0, 2}            # the size classes present in the batch
+    assert all(b in (16, 32, 64) and ms > 0 for b, ms in rep["b"].values())
+    assert rep["ctas_per_sm"][0] in (0, 1)
+    plan = batched.BatchedPlan(mats, b=0, q=1, seed=0)   # the tuned table serves b = 0
+    plan.run()
+    torch.cuda.synchronize()
+    assert int(plan.info.abs().sum()) == 0
+    plan.close()
+    batched.set_tuning([0] * batched.N_CLASSES)  # back to the default
+
+
 @pytest.mark.parametrize("b", [32, 64])
 def test_batched_maximum_sizes(pkg, b):
     """Matrices at the 1024 limit, square and ragged, checked by properties
