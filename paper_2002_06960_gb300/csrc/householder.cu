@@ -9,14 +9,16 @@
 // the reflector of each column needs a reduction over all r rows.  One
 // cooperative grid (one CTA per SM at most) walks the columns; each CTA owns
 // a contiguous slice of rows, held in shared memory when it fits (it does for
-// 16384 x 256 on 152 SMs), else read and written in place through L2.  Three
+// 16384 x 256 on 152 SMs), else read and written in place through L2.  Two
 // bounded grid barriers per column separate
-//   (1) the partial squared norms below the diagonal (and the diagonal entry,
-//       published by the CTA that owns it),
-//   (2) the reflector, identical in every CTA, and the partial dot products
-//       of the reflector with the trailing columns,
-//   (2') the sums of those partials: the CTA k owns the trailing columns
-//       l = j + 1 + k (mod CTAs) and publishes tau * sum,
+//   (1) the partials over own rows below the diagonal of |x|^2 and of
+//       x . A(:, l) for the trailing columns l (x the column below the
+//       diagonal), and row j, published by the CTA that owns it; the
+//       reflector's products follow from these without knowing beta first:
+//       v . A(j:, l) = A(j, l) + (x . A(j+1:, l)) / (alpha - beta);
+//   (2) the reflector, identical in every CTA, and the sums of the partials:
+//       the CTA k owns the trailing columns l = j + 1 + k (mod CTAs) and
+//       publishes tau (v . A(j:, l));
 //   (3) the rank-1 update of every CTA's rows with the published sums.
 // Summing each column's partials once (2') instead of in every CTA keeps the
 // traffic per column at O(CTAs * c) rather than O(CTAs^2 * c).  Every
@@ -38,9 +40,10 @@ struct QrArgs {
   int64_t lda;
   double* W;       // r x c, ld r
   double* tau;     // c
-  double* part1;   // nblocks + 1: partial norms, then the diagonal entry of the column
+  double* part1;   // nblocks: partial squared norms below the diagonal
   double* part2;   // nblocks x c: partial dot products
-  double* tot;     // c: tau * sum of the partial dot products (one writer per column)
+  double* tot;     // c: tau * (v . A(:, l)) of the trailing columns (one writer per column)
+  double* rowj;    // c: row j of the panel, published by the CTA that owns it
   unsigned* bar;   // {count, generation}
   unsigned* err;
 };
@@ -69,23 +72,49 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
 
   // W starts as zero above the diagonal; column j is written in step 3 of j.
   for (int64_t j = 0; j < a.c; ++j) {
-    // ---- (1) partial sum of squares of A(j+1:r, j) over own rows
+    // ---- (1) over own rows below the diagonal, x = A(j+1:r, j): the partial
+    // |x|^2 and the partial products x . A(j+1:r, l) for the trailing columns
+    // l > j.  With v = (1, x / (alpha - beta)) the reflector's products are
+    // v . A(j:r, l) = A(j, l) + (x . A(j+1:r, l)) / (alpha - beta), so these
+    // partials and the row A(j, j:c) are all the exchange the column needs.
+    const int64_t lo = (i0 > j + 1) ? i0 : j + 1;
     double ss = 0.0;
-    {
-      const int64_t lo = (i0 > j + 1) ? i0 : j + 1;
-      for (int64_t i = lo + threadIdx.x; i < i1; i += QR_THREADS) {
+    for (int64_t i = lo + threadIdx.x; i < i1; i += QR_THREADS) {
+      const double x = at(i, j);
+      ss = fma(x, x, ss);
+    }
+    // Each warp takes its columns l = j+1+warp+QR_WARPS*t in groups of 8 and
+    // walks its rows once per group, so the loads of a row are independent
+    // and in flight together.
+    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
+      double d[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) d[t] = 0.0;
+      for (int64_t i = lo + lane; i < i1; i += 32) {
         const double x = at(i, j);
-        ss = fma(x, x, ss);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const int64_t l = l0 + (int64_t)t * QR_WARPS;
+          if (l < a.c) d[t] = fma(x, at(i, l), d[t]);
+        }
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        double y = d[t];
+        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+        const int64_t l = l0 + (int64_t)t * QR_WARPS;
+        if (lane == 0 && l < a.c) a.part2[(int64_t)blockIdx.x * a.c + l] = y;
       }
     }
+    // the CTA that owns row j publishes it
+    if (j >= i0 && j < i1)
+      for (int64_t l = j + threadIdx.x; l < a.c; l += QR_THREADS) a.rowj[l] = at(j, l);
     ss = block_sum(ss, red);
-    if (threadIdx.x == 0) {
-      a.part1[blockIdx.x] = ss;
-      if (j >= i0 && j < i1) a.part1[nb] = at(j, j);
-    }
+    if (threadIdx.x == 0) a.part1[blockIdx.x] = ss;
     if (!grid_barrier(a.bar, nb, a.err, 1, epoch)) return;
 
-    // ---- (2) reflector scalars (every CTA, same order), partial dots
+    // ---- (2) reflector scalars (every CTA, same order), and the sums of the
+    // partials of the columns this CTA owns: l = j + 1 + k (mod CTAs)
     if (warp == 0) {
       // lanes load the partials in parallel; the fixed shuffle tree makes the
       // sum identical in every CTA
@@ -93,7 +122,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
       for (unsigned t = lane; t < nb; t += 32) sig2 += __ldcg(a.part1 + t);
       for (int o = 16; o > 0; o >>= 1) sig2 += __shfl_xor_sync(0xffffffffu, sig2, o);
       if (lane == 0) {
-        const double alpha = __ldcg(a.part1 + nb);
+        const double alpha = __ldcg(a.rowj + j);
         double tau, scale, beta;
         if (sig2 == 0.0) {
           tau = 0.0; beta = alpha; scale = 0.0;
@@ -108,43 +137,16 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
     }
     __syncthreads();
     const double tau = s_coef[0], scale = s_coef[1];
-    // dot_l = sum_{i >= j} v_i A(i, l) for l > j, v_j = 1, v_i = A(i,j) * scale
-    // Each warp takes its columns l = j+1+warp+QR_WARPS*t in groups of 8 and
-    // walks its rows once per group, so the loads of a row are independent
-    // and in flight together.
-    const int64_t lo = (i0 > j) ? i0 : j;
-    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
-      double d[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) d[t] = 0.0;
-      for (int64_t i = lo + lane; i < i1; i += 32) {
-        const double v = (i == j) ? 1.0 : at(i, j) * scale;
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int64_t l = l0 + (int64_t)t * QR_WARPS;
-          if (l < a.c) d[t] = fma(v, at(i, l), d[t]);
-        }
-      }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        double x = d[t];
-        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        const int64_t l = l0 + (int64_t)t * QR_WARPS;
-        if (lane == 0 && l < a.c) a.part2[(int64_t)blockIdx.x * a.c + l] = x;
-      }
+    for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * warp; l < a.c; l += (int64_t)nb * QR_WARPS) {
+      double sp = 0.0;
+      for (unsigned u = lane; u < nb; u += 32) sp += __ldcg(a.part2 + (int64_t)u * a.c + l);
+      for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+      if (lane == 0) a.tot[l] = tau * fma(sp, scale, __ldcg(a.rowj + l));
     }
     if (!grid_barrier(a.bar, nb, a.err, 2, epoch)) return;
 
-    // ---- (2') sums of the partials of the columns this CTA owns
-    for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * warp; l < a.c; l += (int64_t)nb * QR_WARPS) {
-      double s = 0.0;
-      for (unsigned u = lane; u < nb; u += 32) s += __ldcg(a.part2 + (int64_t)u * a.c + l);
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-      if (lane == 0) a.tot[l] = s * tau;
-    }
-    if (!grid_barrier(a.bar, nb, a.err, 3, epoch)) return;
-
     // ---- (3) rank-1 update of own rows, write W(:, j), R(j, j), zeros
+    const int64_t lo3 = (i0 > j) ? i0 : j;
     if (tau != 0.0) {
       for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
         double w[8];
@@ -153,7 +155,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
           const int64_t l = l0 + (int64_t)t * QR_WARPS;
           w[t] = (l < a.c) ? __ldcg(a.tot + l) : 0.0;
         }
-        for (int64_t i = lo + lane; i < i1; i += 32) {
+        for (int64_t i = lo3 + lane; i < i1; i += 32) {
           const double v = (i == j) ? 1.0 : at(i, j) * scale;
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
@@ -182,22 +184,25 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
   }
 }
 
-// Number of CTAs of the panel kernel: at least 64 rows each, at most one per SM
-// not reserved.
+// Number of CTAs of the panel kernel: at least 16 rows each, at most one per SM
+// not reserved.  Every column's FP64 work divides over the CTAs (an SM issues
+// only two DFMA per clock), so short panels, such as the tiles of the
+// by-blocks form, gain from many CTAs of a few rows.
 int qr_blocks(int64_t r, int reserve_sms = 0) {
   int sms = dev_info().sms - reserve_sms;
   if (sms < 1) sms = 1;
-  int nb = (int)((r + 63) / 64);
+  int nb = (int)((r + 15) / 16);
   if (nb > sms) nb = sms;
   if (nb < 1) nb = 1;
   return nb;
 }
 
-// Scratch layout: part1 (SMs + 1), part2 (SMs x c), tot (c), in doubles.
+// Scratch layout: part1 (SMs + 1), part2 (SMs x c), tot (c), rowj (c), in doubles.
 void qr_carve(QrArgs& a, double* base, int sms) {
   a.part1 = base;
   a.part2 = a.part1 + sms + 1;
   a.tot = a.part2 + (size_t)sms * a.c;
+  a.rowj = a.tot + a.c;
 }
 
 int qr_launch(QrArgs& a, int nb, cudaStream_t st) {
@@ -271,7 +276,7 @@ __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const d
 
 size_t householder_scratch_bytes(int64_t c) {
   const int nb = dev_info().sms;
-  return ((size_t)nb + 1 + (size_t)nb * (size_t)c + (size_t)c) * sizeof(double) + 512;
+  return ((size_t)nb + 1 + (size_t)nb * (size_t)c + 2 * (size_t)c) * sizeof(double) + 512;
 }
 
 int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* W, double* tau,
@@ -309,7 +314,7 @@ int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, 
 // library normally takes these from its own growing scratch, which it
 // allocates with cudaMalloc on first use.  This variant keeps them in one
 // fixed array in the library's device image instead, sized for at most
-// kNoAllocMaxSms SMs and kNoAllocMaxCols columns (about 388 KiB).  Every GPU
+// kNoAllocMaxSms SMs and kNoAllocMaxCols columns (about 390 KiB).  Every GPU
 // that loads the library holds that array until the process exits.
 #include <mutex>
 
@@ -319,7 +324,7 @@ namespace {
 constexpr int kNoAllocMaxSms = 192;
 constexpr int kNoAllocMaxCols = 256;
 constexpr size_t kNoAllocPartials =
-    (size_t)kNoAllocMaxSms * (1 + kNoAllocMaxCols) + 1 + kNoAllocMaxCols;
+    (size_t)kNoAllocMaxSms * (1 + kNoAllocMaxCols) + 1 + 2 * kNoAllocMaxCols;
 constexpr size_t kNoAllocBytes = kNoAllocPartials * sizeof(double) + 256;
 
 // Partials first, then 64 status words: [0] error, [1] site, [2..3] barrier.
