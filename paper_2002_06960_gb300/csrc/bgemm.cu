@@ -14,10 +14,14 @@
 //   A is K-major when op(A) = X^T (A(m, k) = X[k + m ldx]) and MN-major when
 //   op(A) = X (A(m, k) = X[m + k ldx]); both are BF16 (kind::f16), for which
 //   the MMA takes either major-ness.
-// Tile 128 x 64 x 64 (BM x BN x BK), cta_group::1; tensor memory holds two
-// accumulator buffers of 128 lanes x 2 BN FP32 columns (the leading product
-// and the correction products of the split).  Warp 0 issues TMA loads (and owns the TMEM
-// allocation), warp 1 issues the MMAs, warps 2-5 drain the accumulator.
+// Tile 128 x 64 x 64 (BM x BN x BK), cta_group::1; tensor memory holds eight
+// accumulators of 128 lanes x BN FP32 columns: two for the leading product
+// A_0 B_0 (one per K step, alternating) and six chains for the correction
+// products of the split (one segment of K steps at a time); a one-pair
+// product spreads each tile over all eight, so that every FP32 accumulation
+// in TMEM stays short.  Warp 0 issues TMA loads (and owns the TMEM allocation), warp 1 issues the
+// MMAs, and warps 2-9 drain the accumulators, two warps per 32-lane quadrant,
+// each on half the columns.
 // Every mbarrier wait is bounded; on timeout the kernel records
 // RANDUTV_ETIMEOUT, lets its copies in flight land, frees TMEM and returns.
 #include <algorithm>
@@ -36,14 +40,20 @@ namespace rutv {
 namespace {
 
 constexpr int BM = 128, BN = 64, BK = 64;
-constexpr int THREADS = 192;
+constexpr int EPI_WARPS = 8;              // two per TMEM lane quadrant
+constexpr int EPI_COLS = BN * 4 / EPI_WARPS;  // columns drained by one epilogue warp
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
+constexpr int CSEG = 16;                  // K steps per correction segment
 constexpr int A_TILE = BM * BK * 2;  // 16 KiB
 constexpr int B_TILE = BN * BK * 2;  // 8 KiB
-constexpr int kTmemCols = 4 * BN;    // two buffers x (leading, correction) accumulators
+constexpr int kCorChains = 6;        // six pairs: correction accumulators
+constexpr int kOneChains = 8;        // one pair: accumulators of a tile
+constexpr int kTmemCols = 8 * BN;    // eight accumulators of BN columns (all of TMEM)
 constexpr int C_ELEMS = BM * BN;     // one output plane tile (mode 1)
 constexpr int C_TILE = C_ELEMS * 2;  // its bytes
-constexpr int C_ROWS = 32;           // rows of one epilogue warp's slice (box C_ROWS x BN)
-constexpr int C_SLICE = C_ROWS * BN; // elements of a slice, column-major (ld C_ROWS)
+constexpr int C_ROWS = 32;           // rows of one quadrant's slice (load box C_ROWS x BN)
+constexpr int C_SLICE = C_ROWS * BN; // elements of a slice, column-major (ld C_ROWS); each
+                                     // epilogue warp stores its half (box C_ROWS x EPI_COLS)
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar,
                                             int x, int y) {
@@ -92,16 +102,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 struct BgemmParams {
   CUtensorMap ta[3];
   CUtensorMap tb[3];
-  CUtensorMap tc[3];   // mode 1: the output planes, box C_ROWS x BN, no swizzle
+  CUtensorMap tc[3];   // mode 1: the output planes, box C_ROWS x BN, no swizzle (loads)
+  CUtensorMap tcs[3];  // mode 1: the same planes, box C_ROWS x EPI_COLS (stores)
   int M, N, K;
   int tiles_n, ntiles, ksteps;
-  int na, nb, npairs;
-  int pair_a[6], pair_b[6];
+  int na, nb, npairs;   // planes of A and B, and pairs (the kernel's template argument)
   int a_mn;            // A MN-major
   int a_x0, a_y0;      // coordinate offsets of A's source (x = source row, y = source col)
   int b_x0, b_y0;
   int stages;
-  int drain_per_tile;  // one-plane products: accumulate the whole K in TMEM, drain once
   int out_upper;       // skip tiles wholly below the diagonal (their C is not wanted)
   int a_upper;         // op(A) upper triangular: K from the tile's first row
   int b_upper;         // B(k, n) = 0 for k > n: K up to the tile's last column
@@ -134,28 +143,49 @@ __device__ __forceinline__ bool tile_range(const BgemmParams& p, int tile, int& 
 }
 
 // Persistent over output tiles (tile t -> rows (t / tiles_n) BM, columns
-// (t % tiles_n) BN).  The tensor-memory accumulator is drained every K step
-// of BK: the MMAs of one step start a fresh accumulator in one of two TMEM
-// buffers, and the epilogue warps add the step's result into a running sum
-// held in registers as an unevaluated FP32 pair (s, c) with a two-sum.  The
-// accumulation inside the tensor core adds each K = 16 product into FP32
-// with a bias, so its error grows like (K / 16) ulp; drained every 64 it
-// stays within a few ulp, and the running sum is exact to about FP32^2.
-// The MMA warp fills one buffer while the other is drained, and the
-// epilogue's output of one tile overlaps the main loop of the next.
+// (t % tiles_n) BN).
+//
+// Six pairs (FP32-level products): the leading product A_0 B_0 starts a fresh
+// TMEM accumulator every K step of BK, alternating between two, and the
+// epilogue warps add each step's result into a running sum held in registers
+// as an unevaluated FP32 pair (s, c) with a two-sum.  The accumulation inside
+// the tensor core adds each K = 16 product into FP32 with a bias, so its
+// error grows like (K / 16) ulp; drained every 64 it stays within a few ulp,
+// and the running sum is exact to about FP32^2.  The five correction
+// products, about 2^-8 of the leading one, accumulate in TMEM over segments
+// of up to CSEG K steps (K = 1024) spread over six chains, so each chain adds
+// about 55 terms and its error stays below 2^-8 x 64 ulp of the result; the
+// epilogue drains them once per segment into the compensation c.
+//
+// One pair (BF16 products): eight chains per tile over all of K, summed once.
+//
+// The epilogue's output of one tile overlaps the main loop of the next.
+// Planes of the split in pair q of the six (i + j <= 2): A_i and B_j.
+__device__ constexpr int pair_a(int q) { return q == 2 || q == 3 ? 1 : (q == 5 ? 2 : 0); }
+__device__ constexpr int pair_b(int q) { return q == 1 || q == 3 ? 1 : (q == 4 ? 2 : 0); }
+
+// NP = 6 (three planes per operand, six pairs) or 1 (one plane): the pair
+// tables, the stage layout and every chain index are compile-time constants,
+// so the MMA warp issues a straight run of tcgen05.mma per K step.
+template <int NP>
 __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant__ BgemmParams p) {
+  static_assert(NP == 1 || NP == 6, "one or six pairs");
+  constexpr int NPL = (NP == 6) ? 3 : 1;          // planes per operand
+  constexpr int per_stage = NPL * (A_TILE + B_TILE);
+  constexpr bool kOnePair = (NP == 1);
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   // 1024-byte aligned tile area
   uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-  const int per_stage = p.na * A_TILE + p.nb * B_TILE;
   // mode 1: the output tile's three planes (column-major BM x BN each) follow the stages
   __nv_bfloat16* ctile = (__nv_bfloat16*)(smem + (size_t)p.stages * per_stage);
   const size_t ctile_bytes = (p.mode == 1) ? (size_t)C_TILE * 3 : 0;
   uint64_t* full = (uint64_t*)(smem + (size_t)p.stages * per_stage + ctile_bytes);
   uint64_t* empty = full + p.stages;
-  uint64_t* acc_full = empty + p.stages;  // [2]
+  uint64_t* acc_full = empty + p.stages;  // [2] lead buffers (six pairs)
   uint64_t* acc_empty = acc_full + 2;     // [2]
-  uint64_t* mma_done = acc_empty + 2;
+  uint64_t* cor_full = acc_empty + 2;     // the chains of a segment (six pairs) or tile (one pair)
+  uint64_t* cor_empty = cor_full + 1;
+  uint64_t* mma_done = cor_empty + 1;
   uint64_t* cfull = mma_done + 1;         // mode 1: output planes loaded
   uint64_t* cfree = cfull + 1;            // mode 1: output planes stored (buffer free)
   uint32_t* tmem_slot = (uint32_t*)(cfree + 1);
@@ -169,11 +199,13 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&acc_full[b], 1);
-      mbar_init(&acc_empty[b], 4);  // one arrival per epilogue warp
+      mbar_init(&acc_empty[b], EPI_WARPS);  // one arrival per epilogue warp
     }
+    mbar_init(cor_full, 1);
+    mbar_init(cor_empty, EPI_WARPS);
     mbar_init(mma_done, 1);
     mbar_init(cfull, 1);
-    mbar_init(cfree, 4);  // one arrival per epilogue warp
+    mbar_init(cfree, EPI_WARPS);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -207,7 +239,8 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
           uint8_t* st = smem + (size_t)s * per_stage;
           mbar_expect_tx(&full[s], (uint32_t)per_stage);
           const int k0 = ks * BK;
-          for (int i = 0; i < p.na; ++i) {
+#pragma unroll
+          for (int i = 0; i < NPL; ++i) {
             uint8_t* dst = st + i * A_TILE;
             if (p.a_mn) {
               tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + m0, p.a_y0 + k0);
@@ -216,8 +249,9 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
               tma_load_2d(dst, &p.ta[i], &full[s], p.a_x0 + k0, p.a_y0 + m0);
             }
           }
-          for (int j = 0; j < p.nb; ++j) {
-            uint8_t* dst = st + p.na * A_TILE + j * B_TILE;
+#pragma unroll
+          for (int j = 0; j < NPL; ++j) {
+            uint8_t* dst = st + NPL * A_TILE + j * B_TILE;
             tma_load_2d(dst, &p.tb[j], &full[s], p.b_x0 + k0, p.b_y0 + n0);
           }
         }
@@ -244,22 +278,30 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
+    // The MMAs of a step go round-robin into several accumulators (chains)
+    // that the epilogue sums: six pairs put A_0 B_0 into the step's lead
+    // buffer and the 20 correction MMAs into six chains; one pair spreads a
+    // tile's MMAs over eight chains.  One thread issues every MMA of the CTA,
+    // and per-MMA work in that thread (indexed parameter loads, descriptor
+    // arithmetic) held the tensor pipe back, so the issue loop is unrolled
+    // with compile-time pairs and chains and each descriptor is one add.
     if (lane == 0) {
       const uint32_t idesc = instr_desc(p.a_mn);
-      int g = 0;
+      // descriptor steps of one K = 16 slice (in 16-byte units) and A's leading offset
+      const int a_kstep = p.a_mn ? 2048 / 16 : 32 / 16;
+      const uint32_t a_lbo = p.a_mn ? (uint32_t)(A_TILE / 2) : 16u;
+      int g = 0;   // K steps over all tiles of this CTA
+      int sg = 0;  // chain groups committed (segments, or tiles for one pair)
       bool run = true;
-      int tl = 0;  // tiles of this CTA
       for (int tile = blockIdx.x; run && tile < p.ntiles; tile += gridDim.x) {
         int m0, n0, kb, ke;
         if (!tile_range(p, tile, m0, n0, kb, ke)) continue;
-        if (p.drain_per_tile) {
-          // one accumulator per tile over all of K, in TMEM buffer tl & 1
-          const int buf = tl & 1, use = tl >> 1;
-          if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), p.err, 16)) {
+        if constexpr (kOnePair) {
+          // chains free once the previous tile's have been drained
+          if (sg > 0 && !mbar_wait(cor_empty, (uint32_t)((sg - 1) & 1), p.err, 16)) {
             run = false;
             break;
           }
-          uint32_t accum = 0u;
           for (int ks = kb; ks < ke; ++ks, ++g) {
             const int s = g % p.stages;
             if (!mbar_wait(&full[s], (uint32_t)((g / p.stages) & 1), p.err, 13)) {
@@ -268,143 +310,184 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t st = smem_u32(smem + (size_t)s * per_stage);
-            const uint32_t b_addr = st + p.na * A_TILE;
+            const uint64_t a0 = smem_desc(st, a_lbo, 1024);
+            const uint64_t b0 = smem_desc(st + A_TILE, 16, 1024);
+            // MMA i of the tile goes to chain i mod 8: steps alternate between
+            // chains 0-3 and 4-7, and the first two steps start them
+            const uint32_t half = (uint32_t)((ks - kb) & 1) * 4u;
+            const uint32_t acc_on = (ks - kb >= 2) ? 1u : 0u;
 #pragma unroll
-            for (int kk = 0; kk < BK / 16; ++kk) {
-              uint64_t ad;
-              if (p.a_mn) ad = smem_desc(st + kk * 2048, A_TILE / 2, 1024);
-              else        ad = smem_desc(st + kk * 32, 16, 1024);
-              const uint64_t bd = smem_desc(b_addr + kk * 32, 16, 1024);
-              mma_bf16(tmem + (uint32_t)(buf * 2 * BN), ad, bd, idesc, accum);
-              accum = 1u;
-            }
+            for (int kk = 0; kk < BK / 16; ++kk)
+              mma_bf16(tmem + (half + (uint32_t)kk) * (uint32_t)BN, a0 + (uint64_t)(kk * a_kstep),
+                       b0 + (uint64_t)(kk * 2), idesc, acc_on);
             mma_commit(&empty[s]);
           }
           if (!run) break;
-          mma_commit(&acc_full[buf]);
-          ++tl;
-          continue;
-        }
-        ++tl;
-        for (int ks = kb; ks < ke; ++ks, ++g) {
-          const int buf = g & 1, use = g >> 1;
-          if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), p.err, 16)) {
-            run = false;
-            break;
-          }
-          const int s = g % p.stages;
-          if (!mbar_wait(&full[s], (uint32_t)((g / p.stages) & 1), p.err, 13)) {
-            run = false;
-            break;
-          }
-          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t st = smem_u32(smem + (size_t)s * per_stage);
-          // Two accumulators per buffer: the leading product A_0 B_0 and the
-          // correction products (about 2^-8 of it), so that the large sum is
-          // rounded once per K term, as in an FP32 GEMM, instead of six times.
-          uint32_t accum[2] = {0u, 0u};
-          for (int q = 0; q < p.npairs; ++q) {
-            const uint32_t a_addr = st + p.pair_a[q] * A_TILE;
-            const uint32_t b_addr = st + p.na * A_TILE + p.pair_b[q] * B_TILE;
-            const int slot = (q == 0) ? 0 : 1;
-#pragma unroll
+          mma_commit(cor_full);
+          ++sg;
+        } else {
+          for (int ks = kb; ks < ke; ++ks, ++g) {
+            const int buf = g & 1, use = g >> 1;
+            const int seg_pos = (ks - kb) % CSEG;
+            const bool seg_end = (seg_pos == CSEG - 1) || (ks == ke - 1);
+            if (use > 0 && !mbar_wait(&acc_empty[buf], (uint32_t)((use - 1) & 1), p.err, 16)) {
+              run = false;
+              break;
+            }
+            if (seg_pos == 0) {
+              // the previous segment's chains must have been drained
+              if (sg > 0 && !mbar_wait(cor_empty, (uint32_t)((sg - 1) & 1), p.err, 20)) {
+                run = false;
+                break;
+              }
+            }
+            const int s = g % p.stages;
+            if (!mbar_wait(&full[s], (uint32_t)((g / p.stages) & 1), p.err, 13)) {
+              run = false;
+              break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t st = smem_u32(smem + (size_t)s * per_stage);
+            const uint64_t a0 = smem_desc(st, a_lbo, 1024);
+            const uint64_t b0 = smem_desc(st + NPL * A_TILE, 16, 1024);
+            const uint32_t fresh = (seg_pos == 0) ? 1u : 0u;  // the segment starts its chains
+  #pragma unroll
             for (int kk = 0; kk < BK / 16; ++kk) {
-              uint64_t ad;
-              if (p.a_mn) ad = smem_desc(a_addr + kk * 2048, A_TILE / 2, 1024);
-              else        ad = smem_desc(a_addr + kk * 32, 16, 1024);
-              const uint64_t bd = smem_desc(b_addr + kk * 32, 16, 1024);
-              mma_bf16(tmem + (uint32_t)((buf * 2 + slot) * BN), ad, bd, idesc, accum[slot]);
-              accum[slot] = 1;
+  #pragma unroll
+              for (int q = 0; q < NP; ++q) {
+                const uint64_t ad = a0 + (uint64_t)((pair_a(q) * A_TILE) >> 4) + (uint64_t)(kk * a_kstep);
+                const uint64_t bd = b0 + (uint64_t)((pair_b(q) * B_TILE + kk * 32) >> 4);
+                if (q == 0) {
+                  mma_bf16(tmem + (uint32_t)(buf * BN), ad, bd, idesc, kk > 0 ? 1u : 0u);
+                } else {
+                  // correction MMA c = 5 kk + q - 1 of the step goes to chain c mod 6
+                  const int c = (NP - 1) * kk + q - 1;
+                  mma_bf16(tmem + (uint32_t)((2 + c % kCorChains) * BN), ad, bd, idesc,
+                           (fresh && c < kCorChains) ? 0u : 1u);
+                }
+              }
+            }
+            mma_commit(&acc_full[buf]);  // the step's leading product is ready
+            mma_commit(&empty[s]);       // stage s is free once these MMAs have read it
+            if (seg_end) {
+              mma_commit(cor_full);      // the segment's corrections are ready
+              ++sg;
             }
           }
-          mma_commit(&empty[s]);         // stage s is free once these MMAs have read it
-          mma_commit(&acc_full[buf]);    // and the step's result is in buffer buf
         }
       }
       mma_commit(mma_done);
     }
   } else {
     // ------------------------------------------------------------ epilogue
-    const int qd = warp & 3;  // TMEM lane quadrant this warp may access
+    const int qd = warp & 3;                          // TMEM lane quadrant this warp may access
+    const int c0 = ((warp - 2) >> 2) * EPI_COLS;      // its columns of the tile (warps 2..)
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
-    int g = 0;
+    int g = 0, sg = 0;
     int tl = 0;  // tiles of this CTA
     bool ok = true;
     for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
       int m0, n0, kb, ke;
       if (!tile_range(p, tile, m0, n0, kb, ke)) continue;
-      float sum[BN], cmp[BN];
+      float sum[EPI_COLS], cmp[EPI_COLS];
 #pragma unroll
-      for (int i = 0; i < BN; ++i) { sum[i] = 0.f; cmp[i] = 0.f; }
-      if (p.drain_per_tile) {
-        const int buf = tl & 1, use = tl >> 1;
-        bool w = mbar_wait(&acc_full[buf], (uint32_t)(use & 1), p.err, 14);
+      for (int i = 0; i < EPI_COLS; ++i) { sum[i] = 0.f; cmp[i] = 0.f; }
+      if (kOnePair) {
+        // the chains that received MMAs (fewer than kOneChains when K is short)
+        const int nch = min(kOneChains, (BK / 16) * (ke - kb));
+        bool w = mbar_wait(cor_full, (uint32_t)(sg & 1), p.err, 14);
         ok = __all_sync(0xffffffffu, w) && ok;
         if (!ok) break;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        for (int ch = 0; ch < nch; ++ch) {
+          float v[EPI_COLS];
 #pragma unroll
-        for (int cc = 0; cc < BN; cc += 32) tmem_ld32(tmem + lane_base + (uint32_t)(buf * 2 * BN + cc), sum + cc);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
-      }
-      for (int ks = kb; !p.drain_per_tile && ks < ke; ++ks, ++g) {
-        const int buf = g & 1, use = g >> 1;
-        bool w = mbar_wait(&acc_full[buf], (uint32_t)(use & 1), p.err, 14);
-        ok = __all_sync(0xffffffffu, w) && ok;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int cc = 0; cc < EPI_COLS; cc += 32)
+            tmem_ld32(tmem + lane_base + (uint32_t)(ch * BN + c0 + cc), v + cc);
 #pragma unroll
-        for (int cc = 0; cc < BN; cc += 32) {
-          float v[32];
-          tmem_ld32(tmem + lane_base + (uint32_t)(buf * 2 * BN + cc), v);
-          if (p.npairs > 1) {
-            float lo[32];
-            tmem_ld32(tmem + lane_base + (uint32_t)((buf * 2 + 1) * BN + cc), lo);
-#pragma unroll
-            for (int i = 0; i < 32; ++i) v[i] += lo[i];
-          }
-#pragma unroll
-          for (int i = 0; i < 32; ++i) {
-            float t, e;
-            two_sum(sum[cc + i], v[i], t, e);
-            sum[cc + i] = t;
-            cmp[cc + i] += e;
-          }
+          for (int i = 0; i < EPI_COLS; ++i) sum[i] += v[i];
         }
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
-        if (lane == 0) mbar_arrive(&acc_empty[buf]);
+        if (lane == 0) mbar_arrive(cor_empty);
+        ++sg;
+      }
+      for (int ks = kb; !kOnePair && ks < ke; ++ks, ++g) {
+        const int buf = g & 1, use = g >> 1;
+        const int seg_pos = (ks - kb) % CSEG;
+        const bool seg_end = (seg_pos == CSEG - 1) || (ks == ke - 1);
+        bool w = mbar_wait(&acc_full[buf], (uint32_t)(use & 1), p.err, 14);
+        ok = __all_sync(0xffffffffu, w) && ok;
+        if (!ok) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float v[EPI_COLS];
+#pragma unroll
+        for (int cc = 0; cc < EPI_COLS; cc += 32)
+          tmem_ld32(tmem + lane_base + (uint32_t)(buf * BN + c0 + cc), v + cc);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&acc_empty[buf]);  // the buffer is free again
+#pragma unroll
+        for (int i = 0; i < EPI_COLS; ++i) {
+          float t, e;
+          two_sum(sum[i], v[i], t, e);
+          sum[i] = t;
+          cmp[i] += e;
+        }
+        if (seg_end) {
+          w = mbar_wait(cor_full, (uint32_t)(sg & 1), p.err, 21);
+          ok = __all_sync(0xffffffffu, w) && ok;
+          if (!ok) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int ch = 0; ch < kCorChains; ++ch) {
+#pragma unroll
+            for (int cc = 0; cc < EPI_COLS; cc += 32)
+              tmem_ld32(tmem + lane_base + (uint32_t)((2 + ch) * BN + c0 + cc), v + cc);
+#pragma unroll
+            for (int i = 0; i < EPI_COLS; ++i) cmp[i] += v[i];
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(cor_empty);
+          ++sg;
+        }
       }
       // warp-uniform: the lanes must not split before the next tcgen05.ld
       if (__any_sync(0xffffffffu, !ok || *(volatile unsigned*)p.err != 0)) break;
-      // the tile's sum, rounded once to FP32 (frees the compensation registers)
+      // the tile's sum, rounded once to FP32
 #pragma unroll
-      for (int i = 0; i < BN; ++i) sum[i] += cmp[i];
+      for (int i = 0; i < EPI_COLS; ++i) sum[i] += cmp[i];
       const int row = m0 + qd * 32 + lane;
       if (row < p.M) {
         if (p.mode == 0) {
+          // read this row's C first: a store may alias the next column's
+          // load, so interleaved they would wait one by one
+          float* crow = p.C + (int64_t)row + (int64_t)(n0 + c0) * p.ldc;
+          const int ncol = min(EPI_COLS, p.N - (n0 + c0));
+          if (p.beta != 0.f) {
+            float cv[EPI_COLS];
 #pragma unroll
-          for (int i = 0; i < BN; ++i) {
-            const int col = n0 + i;
-            if (col < p.N) {
-              float* dst = p.C + (int64_t)row + (int64_t)col * p.ldc;
-              float r = p.alpha * sum[i];
-              if (p.beta != 0.f) r = fmaf(p.beta, *dst, r);
-              *dst = r;
-            }
+            for (int i = 0; i < EPI_COLS; ++i) cv[i] = (i < ncol) ? crow[(int64_t)i * p.ldc] : 0.f;
+#pragma unroll
+            for (int i = 0; i < EPI_COLS; ++i) sum[i] = fmaf(p.beta, cv[i], p.alpha * sum[i]);
+          } else {
+#pragma unroll
+            for (int i = 0; i < EPI_COLS; ++i) sum[i] *= p.alpha;
           }
+#pragma unroll
+          for (int i = 0; i < EPI_COLS; ++i)
+            if (i < ncol) crow[(int64_t)i * p.ldc] = sum[i];
         }
       }
       if (p.mode == 1) {
-        // this warp's 32 rows of the tile's planes, in shared memory (zero
-        // past the matrix edge); each warp stores its own slice back, so the
-        // epilogue warps never wait on one another
+        // this warp's 32 rows x EPI_COLS columns of the tile's planes, in shared
+        // memory (zero past the matrix edge); each warp stores its own block
+        // back, so the epilogue warps never wait on one another
         const bool w = mbar_wait(cfull, (uint32_t)(tl & 1), p.err, 19);
         if (__any_sync(0xffffffffu, !w)) break;
-        __nv_bfloat16* sl0 = ctile + (size_t)qd * C_SLICE;
+        __nv_bfloat16* sl0 = ctile + (size_t)qd * C_SLICE + (size_t)c0 * C_ROWS;
 #pragma unroll
-        for (int i = 0; i < BN; ++i) {
+        for (int i = 0; i < EPI_COLS; ++i) {
           const int o = i * C_ROWS + lane;
           // X + alpha acc carried as hi + lo, then split into three planes
           const float x0 = __bfloat162float(sl0[o]);
@@ -426,9 +509,9 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
         __syncwarp();
         if (lane == 0) {
           for (int i = 0; i < 3; ++i)
-            tma_store_2d(&p.tc[i], sl0 + (size_t)i * C_ELEMS, m0 + qd * C_ROWS, n0);
+            tma_store_2d(&p.tcs[i], sl0 + (size_t)i * C_ELEMS, m0 + qd * C_ROWS, n0 + c0);
           bulk_commit();
-          bulk_wait_read();  // this slice may be overwritten from here on
+          bulk_wait_read();  // this block may be overwritten from here on
           mbar_arrive(cfree);
         }
         __syncwarp();
@@ -529,13 +612,9 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.N = N;
   p.K = K;
   if (pairs_mode == 3 && p.na == 3 && p.nb == 3) {
-    const int pa[6] = {0, 0, 1, 1, 0, 2}, pb[6] = {0, 1, 0, 1, 2, 0};
-    p.npairs = 6;
-    for (int i = 0; i < 6; ++i) { p.pair_a[i] = pa[i]; p.pair_b[i] = pb[i]; }
+    p.npairs = 6;  // the pairs i + j <= 2 (pair_a, pair_b)
   } else {
     p.npairs = 1;
-    p.pair_a[0] = 0;
-    p.pair_b[0] = 0;
     p.na = p.nb = 1;
   }
   p.a_mn = A.mn_major;
@@ -552,9 +631,12 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.stages = stages;
   p.mode = out.mode;
   if (out.mode == 1) {
-    for (int i = 0; i < 3; ++i)
+    for (int i = 0; i < 3; ++i) {
       RUTV_TRY(make_tmap_box(&p.tc[i], out.planes[i], M, N, out.ldp, C_ROWS, BN,
                              CU_TENSOR_MAP_SWIZZLE_NONE));
+      RUTV_TRY(make_tmap_box(&p.tcs[i], out.planes[i], M, N, out.ldp, C_ROWS, EPI_COLS,
+                             CU_TENSOR_MAP_SWIZZLE_NONE));
+    }
   }
   p.alpha = out.alpha;
   p.beta = out.beta;
@@ -569,7 +651,6 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.tiles_n = (N + BN - 1) / BN;
   p.ntiles = tiles_m * p.tiles_n;
   p.ksteps = (K + BK - 1) / BK;
-  p.drain_per_tile = (p.npairs == 1) ? 1 : 0;
   p.out_upper = tri.out_upper;
   p.a_upper = tri.a_upper;
   p.b_upper = tri.b_upper;
@@ -591,8 +672,9 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
       mma_flops += 2.0 * rows * cols * kk * p.npairs;
     }
   }
-  const size_t smem = 1024 + (size_t)stages * per_stage + ctile_bytes + (2 * stages + 7) * 8 + 16;
-  RUTV_TRY(ensure_smem((const void*)bgemm_kernel, smem));
+  const size_t smem = 1024 + (size_t)stages * per_stage + ctile_bytes + (2 * stages + 11) * 8 + 16;
+  const void* fn = (p.npairs == 6) ? (const void*)bgemm_kernel<6> : (const void*)bgemm_kernel<1>;
+  RUTV_TRY(ensure_smem(fn, smem));
   // persistent: at most one CTA per SM (the shared memory allows no more)
   int cap = dev_info().sms;
   if (max_ctas > 0 && max_ctas < cap) cap = max_ctas;
@@ -601,7 +683,8 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
                  2.0 * ((double)M * K * p.na + (double)K * N * p.nb) +
                      (out.mode == 0 ? 4.0 : 12.0) * M * (double)N,
                  st);
-  bgemm_kernel<<<grid, THREADS, smem, st>>>(p);
+  if (p.npairs == 6) bgemm_kernel<6><<<grid, THREADS, smem, st>>>(p);
+  else bgemm_kernel<1><<<grid, THREADS, smem, st>>>(p);
   note_launch();
   RUTV_CK(cudaGetLastError());
   return 0;

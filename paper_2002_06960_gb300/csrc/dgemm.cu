@@ -9,6 +9,7 @@
 // tiles, 4 x 4 accumulators per thread (16 independent chains), operands
 // staged through shared memory, and a deterministic split-K (partials summed
 // in a fixed order) when the output has too few tiles to cover the SMs.
+#include <algorithm>
 #include <cmath>
 
 #include "common.cuh"
@@ -22,12 +23,13 @@ template <bool TA, bool TB>
 __global__ void __launch_bounds__(NT)
 dgemm_kernel(int64_t M, int64_t N, int64_t K, int64_t kchunk, double alpha,
              const double* __restrict__ A, int64_t lda, const double* __restrict__ B, int64_t ldb,
-             double beta, double* __restrict__ C, int64_t ldc, double* __restrict__ P) {
+             double beta, double* __restrict__ C, int64_t ldc, double* __restrict__ P, bool lower) {
   __shared__ double As[BK][BM + 1];
   __shared__ double Bs[BK][BN + 1];
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
   const int64_t m0 = (int64_t)blockIdx.x * BM, n0 = (int64_t)blockIdx.y * BN;
+  if (lower && n0 >= m0 + BM) return;  // tile wholly above the diagonal: not wanted
   const int64_t kb = (int64_t)blockIdx.z * kchunk;
   const int64_t ke = (kb + kchunk < K) ? kb + kchunk : K;
 
@@ -108,15 +110,17 @@ dgemm_kernel(int64_t M, int64_t N, int64_t K, int64_t kchunk, double alpha,
 }
 
 // C = alpha * sum_z P[z] + beta * C, summed in the order z = 0, 1, ...
+// (lower: only the elements of the tiles the product computed).
 __global__ void splitk_reduce_kernel(int64_t M, int64_t N, int splits, double alpha,
                                      const double* __restrict__ P, double beta,
-                                     double* __restrict__ C, int64_t ldc) {
+                                     double* __restrict__ C, int64_t ldc, bool lower) {
   const int64_t MN = M * N;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < MN;
        e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t m = e % M, n = e / M;
+    if (lower && (n / BN) * BN >= (m / BM) * BM + BM) continue;
     double s = 0.0;
     for (int z = 0; z < splits; ++z) s += P[z * MN + e];
-    const int64_t m = e % M, n = e / M;
     double v = alpha * s;
     if (beta != 0.0) v = fma(beta, C[m + n * ldc], v);
     C[m + n * ldc] = v;
@@ -162,10 +166,24 @@ static int choose_splits(int64_t tiles, int64_t M, int64_t N, int64_t K, int sms
 
 int launch_dgemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha,
                  const double* A, int64_t lda, const double* B, int64_t ldb, double beta,
-                 double* C, int64_t ldc, double* scratch, size_t scratch_bytes, cudaStream_t st) {
+                 double* C, int64_t ldc, double* scratch, size_t scratch_bytes, cudaStream_t st,
+                 bool lower) {
   if (M <= 0 || N <= 0) return 0;
   const int64_t tm = (M + BM - 1) / BM, tn = (N + BN - 1) / BN;
-  const int64_t tiles = tm * tn;
+  // tiles computed (lower: those that meet or lie below the diagonal) and their elements
+  int64_t tiles = tm * tn;
+  double elems = (double)M * (double)N;
+  if (lower) {
+    tiles = 0;
+    elems = 0.0;
+    for (int64_t i = 0; i < tm; ++i) {
+      const int64_t rows = std::min<int64_t>(BM, M - i * BM);
+      for (int64_t j = 0; j < tn && j * BN < i * BM + BM; ++j) {
+        ++tiles;
+        elems += (double)rows * (double)std::min<int64_t>(BN, N - j * BN);
+      }
+    }
+  }
   const int sms = dev_info().sms;
   int splits = scratch ? choose_splits(tiles, M, N, K, sms, scratch_bytes) : 1;
   int64_t kchunk = K;
@@ -175,12 +193,12 @@ int launch_dgemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
     splits = (int)((K + kchunk - 1) / kchunk);
   }
   if (K <= 0) kchunk = 0;
-  ProfScope prof(K_DGEMM, 2.0 * (double)M * (double)N * (double)K,
-                 8.0 * ((double)M * K + (double)K * N + (double)M * N * (beta != 0.0 ? 2 : 1)), st);
+  ProfScope prof(K_DGEMM, 2.0 * elems * (double)K,
+                 8.0 * ((double)M * K + (double)K * N + elems * (beta != 0.0 ? 2 : 1)), st);
   dim3 grid((unsigned)tm, (unsigned)tn, (unsigned)splits);
   double* P = splits > 1 ? scratch : nullptr;
 #define RUTV_DG(TA_, TB_) \
-  dgemm_kernel<TA_, TB_><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, P)
+  dgemm_kernel<TA_, TB_><<<grid, NT, 0, st>>>(M, N, K, kchunk, alpha, A, lda, B, ldb, beta, C, ldc, P, lower)
   if (!ta && !tb) RUTV_DG(false, false);
   else if (!ta && tb) RUTV_DG(false, true);
   else if (ta && !tb) RUTV_DG(true, false);
@@ -192,7 +210,8 @@ int launch_dgemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha
     int64_t n = M * N;
     int64_t blocks = (n + 255) / 256;
     if (blocks > 8 * sms) blocks = 8 * sms;
-    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(M, N, splits, alpha, P, beta, C, ldc);
+    splitk_reduce_kernel<<<(unsigned)blocks, 256, 0, st>>>(M, N, splits, alpha, P, beta, C, ldc,
+                                                            lower);
     note_launch();
     RUTV_CK(cudaGetLastError());
   }

@@ -221,7 +221,7 @@ int qr_launch(QrArgs& a, int nb, cudaStream_t st) {
   return 0;
 }
 
-// S (c x c, ld c) from the Gram matrix Gm = W^T W (c x c, ld c) and tau, the
+// S (c x c, ld c) from the Gram matrix Gm = W^T W (c x c, ld ldg) and tau, the
 // compact-WY factor of H_1 ... H_c = I - W S W^T (forward, column-wise):
 // S_jj = tau_j, S(0:j, j) = -tau_j S(0:j, 0:j) Gm(0:j, j).
 // That recurrence is the inverse of the upper triangle striu(Gm) + diag(1/tau)
@@ -230,11 +230,13 @@ int qr_launch(QrArgs& a, int nb, cudaStream_t st) {
 // which also gives the zero rows and columns of reflectors with tau = 0.
 // One warp per column k, S(:, k) in shared memory; Gm(i, l) is read as
 // Gm(l, i) (Gm is symmetric) so that the lanes read contiguous memory, and
-// the next row's operands are loaded while the current row is reduced.
+// the next row's operands are loaded while the current row is reduced.  Only
+// the strictly lower part of Gm is read (the diagonal enters through tau).
 constexpr int WY_WARPS = 8;
 constexpr int WY_MAXC = 256;
 
 __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const double* __restrict__ Gm,
+                                                                   int64_t ldg,
                                                                    const double* __restrict__ tau,
                                                                    double* __restrict__ S) {
   __shared__ double col[WY_WARPS][WY_MAXC];
@@ -249,7 +251,7 @@ __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const d
 #pragma unroll
     for (int t = 0; t < NL; ++t) {
       const int l = i + 1 + lane + 32 * t;
-      g[t] = (i >= 0 && l <= k) ? Gm[l + (int64_t)i * c] : 0.0;
+      g[t] = (i >= 0 && l <= k) ? Gm[l + (int64_t)i * ldg] : 0.0;
     }
   };
   load_row(k, gcur);
@@ -293,12 +295,15 @@ int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* 
   return qr_launch(a, nb, st);
 }
 
-int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st) {
+int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st,
+                     int64_t ldg) {
   if (c <= 0) return 0;
   if (c > WY_MAXC) return RANDUTV_EUNSUPPORTED;
+  if (ldg == 0) ldg = c;
+  if (ldg < c) return RANDUTV_EUNSUPPORTED;
   ProfScope prof(K_WY, (double)c * c * c / 3.0, 16.0 * (double)c * c, st);
   wy_factor_kernel<<<(unsigned)((c + WY_WARPS - 1) / WY_WARPS), WY_WARPS * 32, 0, st>>>((int)c, Gm,
-                                                                                        tau, S);
+                                                                                        ldg, tau, S);
   note_launch();
   RUTV_CK(cudaGetLastError());
   return 0;

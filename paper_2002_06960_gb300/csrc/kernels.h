@@ -17,9 +17,12 @@ int launch_philox_normal_rows(uint64_t seed, uint32_t step, uint32_t mid, uint32
 int launch_philox_words(uint64_t seed, uint4 c, int64_t count, uint32_t* out, cudaStream_t st);
 
 size_t dgemm_scratch_bytes(int64_t M, int64_t N);
+// lower: compute only the 64 x 64 tiles of C that meet or lie below the
+// diagonal (for a symmetric product whose reader takes its lower triangle);
+// the others are left as they were.
 int launch_dgemm(bool ta, bool tb, int64_t M, int64_t N, int64_t K, double alpha, const double* A,
                  int64_t lda, const double* B, int64_t ldb, double beta, double* C, int64_t ldc,
-                 double* scratch, size_t scratch_bytes, cudaStream_t st);
+                 double* scratch, size_t scratch_bytes, cudaStream_t st, bool lower = false);
 
 size_t householder_scratch_bytes(int64_t c);
 // SMs that the small SVD may hold while it runs beside a block step.
@@ -28,7 +31,10 @@ constexpr int kSvdSms = 16;
 int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* W, double* tau,
                           char* scratch, unsigned* bar, unsigned* err, cudaStream_t st,
                           int reserve_sms = 0);
-int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st);
+// S (c x c, ld c) from the Gram matrix of the reflectors (its diagonal and
+// strictly lower part are read, leading dimension ldg; 0 means c) and tau.
+int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st,
+                     int64_t ldg = 0);
 
 // Scratch of launch_small_svd (beside the dgemm scratch it also takes).
 size_t small_svd_scratch_bytes(int b);

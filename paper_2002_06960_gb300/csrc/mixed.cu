@@ -37,9 +37,10 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ src, int64_t lds, in
 }
 
 // tau_j <- 2 / Gm(j, j) for the reflectors that are not the identity (tau_j = 0).
-__global__ void retau_kernel(int c, const double* __restrict__ Gm, double* __restrict__ tau) {
+__global__ void retau_kernel(int c, const double* __restrict__ Gm, int64_t ldg,
+                             double* __restrict__ tau) {
   for (int j = threadIdx.x; j < c; j += blockDim.x)
-    if (tau[j] != 0.0) tau[j] = 2.0 / Gm[j + (int64_t)j * c];
+    if (tau[j] != 0.0) tau[j] = 2.0 / Gm[j + (int64_t)j * ldg];
 }
 
 int grid_of(int64_t total) {
@@ -256,21 +257,18 @@ struct MCtx {
   int cap() const { return svd_live ? dev_info().sms - kSvdSms : 0; }
 };
 
-// From the FP64 reflectors W64 (r x bi) and tau: W planes, S (FP64), and
+// From the rounded reflectors (W64 = W~, r x bi, and their planes), tau and
+// the lower triangle of their Gram W~^T W~ (left by mixed_qr): S (FP64), and
 // WSt = (W S^T)^T as planes (bi x r).
 //
 // The reflectors the updates apply are the rounded W~ held in the planes.  S
-// is built from W~ itself: its Gram W~^T W~ in FP64 (over r terms; an FP32
+// is built from W~ itself: its Gram in FP64 (over r terms; an FP32
 // accumulation would be off by about sqrt(r) ulp) and tau~_j = 2 / |w~_j|^2,
 // so that every H_j = I - tau~_j w~_j w~_j^T, and with them I - W~ S W~^T,
 // is orthogonal to FP64 accuracy rather than to the accuracy of the rounding.
 int mixed_wy(MCtx& c, int64_t r, int64_t bi) {
   MixedWork& w = c.w;
-  RUTV_TRY(split_f64(w.W64, r, r, bi, 0, w.W, 0, 0, c.st));
-  RUTV_TRY(merge_f64(w.W, 0, 0, r, bi, 0, w.W64, r, c.st));
-  RUTV_TRY(launch_dgemm(true, false, bi, bi, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, bi, w.dgemm,
-                        w.dgemm_bytes, c.st));
-  retau_kernel<<<1, 256, 0, c.st>>>((int)bi, w.Gram64, w.tau);
+  retau_kernel<<<1, 256, 0, c.st>>>((int)bi, w.Gram64, bi, w.tau);
   note_launch();
   RUTV_CK(cudaGetLastError());
   RUTV_TRY(launch_wy_factor(bi, w.Gram64, w.tau, w.S64, c.st));
@@ -297,26 +295,47 @@ int mixed_apply_transposed(MCtx& c, const Planes& Xt, int64_t k, int64_t r, int6
   return 0;
 }
 
-// Householder QR (FP64) of the panel P (r x bi, ld r) into W64 (ld r) and
-// tau.  Panels of more than 128 columns are factored in two halves: the QR
-// of the first h = 128 columns, their block reflector applied to the rest,
-// P2 <- (I - W1 S1 W1^T)^T P2 (FP64 products, S1 from the FP64 Gram of W1),
-// and the QR of P2 below row h.  The reflectors are those of the unblocked
-// factorization (up to rounding order); each half keeps its rows in shared
-// memory where the whole panel would not fit, and its columns see at most
-// 127 trailing columns.
+// Rounds the reflectors W64(:, c0:c0+nc) to their planes (columns c0: of W)
+// and writes the rounded values back, so that W64 holds W~ from here on.
+int mixed_round_w(MCtx& c, int64_t r, int64_t c0, int64_t nc) {
+  MixedWork& w = c.w;
+  RUTV_TRY(split_f64(w.W64 + c0 * r, r, r, nc, 0, w.W, 0, c0, c.st));
+  return merge_f64(w.W, 0, c0, r, nc, 0, w.W64 + c0 * r, r, c.st);
+}
+
+// Householder QR (FP64) of the panel P (r x bi, ld r) into the rounded
+// reflectors W~ (W64, ld r, and the planes W), tau, and the lower triangle of
+// the Gram W~^T W~ (Gram64, ld bi) that mixed_wy needs.  Panels of more than
+// 128 columns are factored in two halves: the QR of the first h = 128
+// columns, whose rounded block reflector I - W~1 S1 W~1^T (S1 from the
+// Gram's leading block, tau~ = 2 / |w~|^2) is applied to the rest in FP64,
+// P2 <- (I - W~1 S1 W~1^T)^T P2, then the QR of P2 below row h.  The
+// reflectors are those of the unblocked factorization up to rounding; each
+// half keeps its rows in shared memory where the whole panel would not fit,
+// and its columns see at most 127 trailing columns.  The Gram is built by
+// blocks: the leading block before the second half, then the blocks of the
+// second half's reflectors over rows h: (above them W~2 is zero), and only
+// the tiles on or below the diagonal of the symmetric blocks.
 int mixed_qr(MCtx& c, int64_t r, int64_t bi, double* P, int reserve) {
   MixedWork& w = c.w;
   constexpr int64_t h = 128;
-  if (bi <= h || r - h < bi - h)
-    return launch_householder_qr(r, bi, P, r, w.W64, w.tau, w.qr, c.status + 2, c.status, c.st,
-                                 reserve);
+  if (bi <= h || r - h < bi - h) {
+    RUTV_TRY(launch_householder_qr(r, bi, P, r, w.W64, w.tau, w.qr, c.status + 2, c.status, c.st,
+                                   reserve));
+    RUTV_TRY(mixed_round_w(c, r, 0, bi));
+    return launch_dgemm(true, false, bi, bi, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, bi, w.dgemm,
+                        w.dgemm_bytes, c.st, true);
+  }
   const int64_t h2 = bi - h;
   RUTV_TRY(launch_householder_qr(r, h, P, r, w.W64, w.tau, w.qr, c.status + 2, c.status, c.st,
                                  reserve));
-  RUTV_TRY(launch_dgemm(true, false, h, h, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, h, w.dgemm,
-                        w.dgemm_bytes, c.st));
-  RUTV_TRY(launch_wy_factor(h, w.Gram64, w.tau, w.S64, c.st));
+  RUTV_TRY(mixed_round_w(c, r, 0, h));
+  RUTV_TRY(launch_dgemm(true, false, h, h, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, bi, w.dgemm,
+                        w.dgemm_bytes, c.st, true));
+  retau_kernel<<<1, 256, 0, c.st>>>((int)h, w.Gram64, bi, w.tau);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  RUTV_TRY(launch_wy_factor(h, w.Gram64, w.tau, w.S64, c.st, bi));
   double* P2 = P + h * r;
   RUTV_TRY(launch_dgemm(true, false, h, h2, r, 1.0, w.W64, r, P2, r, 0.0, w.qrX, h, w.dgemm,
                         w.dgemm_bytes, c.st));
@@ -326,12 +345,17 @@ int mixed_qr(MCtx& c, int64_t r, int64_t bi, double* P, int reserve) {
                         w.dgemm_bytes, c.st));
   RUTV_TRY(launch_householder_qr(r - h, h2, P2 + h, r, w.W2, w.tau + h, w.qr, c.status + 2,
                                  c.status, c.st, reserve));
-  // W(:, h:) = [0; W2]
+  // W(:, h:) = [0; W2], rounded
   double* Wr = w.W64 + h * r;
   RUTV_CK(cudaMemset2DAsync(Wr, (size_t)r * 8, 0, (size_t)h * 8, (size_t)h2, c.st));
   RUTV_CK(cudaMemcpy2DAsync(Wr + h, (size_t)r * 8, w.W2, (size_t)(r - h) * 8, (size_t)(r - h) * 8,
                             (size_t)h2, cudaMemcpyDeviceToDevice, c.st));
-  return 0;
+  RUTV_TRY(mixed_round_w(c, r, h, h2));
+  // Gram(h:, :h) = W~2^T W~1 and the lower part of Gram(h:, h:) = W~2^T W~2, rows h: only
+  RUTV_TRY(launch_dgemm(true, false, h2, h, r - h, 1.0, Wr + h, r, w.W64 + h, r, 0.0, w.Gram64 + h,
+                        bi, w.dgemm, w.dgemm_bytes, c.st));
+  return launch_dgemm(true, false, h2, h2, r - h, 1.0, Wr + h, r, Wr + h, r, 0.0,
+                      w.Gram64 + h + h * bi, bi, w.dgemm, w.dgemm_bytes, c.st, true);
 }
 
 // Joins the side stream and applies the pending row folds
