@@ -32,7 +32,8 @@ namespace rutv {
 namespace {
 constexpr int QR_THREADS = 256;
 constexpr int QR_WARPS = QR_THREADS / 32;
-constexpr size_t kQrSmemMax = 220 * 1024;  // own rows kept in shared memory up to this size
+constexpr size_t kQrSmemMax = 216 * 1024;  // own rows kept in shared memory up to this size
+constexpr int kOwnMax = 37;  // owned columns per warp: ceil(255 / 7) with one CTA, c <= 256
 
 struct QrArgs {
   int64_t r, c;
@@ -53,6 +54,9 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
   extern __shared__ double smA[];  // kSmem: own rows, column-major, ld rows_per
   __shared__ double red[QR_WARPS];
   __shared__ double s_coef[4];  // tau, scale, beta
+  // owned columns' (sum of partials, A(j, l)) per warp 1..: at most
+  // ceil((c - 1) / ((QR_WARPS - 1) nb)) each (checked on the host)
+  __shared__ double s_own[QR_WARPS - 1][kOwnMax][2];
   const unsigned nb = gridDim.x;
   const int64_t rows_per = (a.r + nb - 1) / nb;
   const int64_t i0 = (int64_t)blockIdx.x * rows_per;
@@ -114,7 +118,9 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
     if (!grid_barrier(a.bar, nb, a.err, 1, epoch)) return;
 
     // ---- (2) reflector scalars (every CTA, same order), and the sums of the
-    // partials of the columns this CTA owns: l = j + 1 + k (mod CTAs)
+    // partials of the columns this CTA owns: l = j + 1 + k (mod CTAs).  Warp 0
+    // reduces |x|^2 while warps 1.. load and sum the owned columns' partials
+    // (they do not depend on the reflector), so the two L2 round trips overlap.
     if (warp == 0) {
       // lanes load the partials in parallel; the fixed shuffle tree makes the
       // sum identical in every CTA
@@ -135,13 +141,26 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
         s_coef[0] = tau; s_coef[1] = scale; s_coef[2] = beta;
       }
     }
+    else {
+      int t = 0;
+      for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * (warp - 1); l < a.c;
+           l += (int64_t)nb * (QR_WARPS - 1), ++t) {
+        double sp = 0.0;
+        for (unsigned u = lane; u < nb; u += 32) sp += __ldcg(a.part2 + (int64_t)u * a.c + l);
+        for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
+        if (lane == 0) {
+          s_own[warp - 1][t][0] = sp;
+          s_own[warp - 1][t][1] = __ldcg(a.rowj + l);
+        }
+      }
+    }
     __syncthreads();
     const double tau = s_coef[0], scale = s_coef[1];
-    for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * warp; l < a.c; l += (int64_t)nb * QR_WARPS) {
-      double sp = 0.0;
-      for (unsigned u = lane; u < nb; u += 32) sp += __ldcg(a.part2 + (int64_t)u * a.c + l);
-      for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
-      if (lane == 0) a.tot[l] = tau * fma(sp, scale, __ldcg(a.rowj + l));
+    if (warp > 0 && lane == 0) {
+      int t = 0;
+      for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * (warp - 1); l < a.c;
+           l += (int64_t)nb * (QR_WARPS - 1), ++t)
+        a.tot[l] = tau * fma(s_own[warp - 1][t][0], scale, s_own[warp - 1][t][1]);
     }
     if (!grid_barrier(a.bar, nb, a.err, 2, epoch)) return;
 
@@ -206,6 +225,7 @@ void qr_carve(QrArgs& a, double* base, int sms) {
 }
 
 int qr_launch(QrArgs& a, int nb, cudaStream_t st) {
+  if (a.c - 1 > (int64_t)(QR_WARPS - 1) * nb * kOwnMax) return RANDUTV_EUNSUPPORTED;
   const int64_t rows_per = (a.r + nb - 1) / nb;
   const size_t smem = (size_t)rows_per * (size_t)a.c * sizeof(double);
   void* args[] = {&a};

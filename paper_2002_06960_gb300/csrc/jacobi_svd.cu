@@ -6,7 +6,9 @@
 //      its columns are orthogonal to FP32 accuracy, the rotations accumulated
 //      in V32.  FP32 runs at 64 times the FP64 rate of this part, and the
 //      sweeps that take a dense block to near-orthogonal columns are most of
-//      the work.
+//      the work.  They run by blocks of columns (block_jacobi_f32_kernel),
+//      so that a cluster barrier comes once per block pair rather than twice
+//      per round of column pairs.
 //   2. V32 is made orthogonal to FP64 accuracy by two Newton-Schulz steps
 //      V <- V (3I - V^T V) / 2 (FP64 products), C = B V in FP64, and FP64
 //      sweeps on C that start from V finish the job.  The columns of C are
@@ -16,7 +18,7 @@
 //      not depend on phase 1 beyond rounding.
 // Blocks of at most 32 columns skip phase 1.
 //
-// Both phases run one kernel, templated on the arithmetic type, on one
+// Phase 2 runs jacobi_kernel (templated on the arithmetic type) on one
 // thread-block cluster of C CTAs.  CTA k holds rows [k R, (k+1) R) of the
 // working matrix and of V in shared memory.  A sweep is b-1 rounds of the
 // round-robin (circle) ordering, each rotating b/2 disjoint column pairs:
@@ -73,7 +75,6 @@ size_t jac_smem_bytes(int b, int ncl) {
          + 2 * (size_t)P * sizeof(int) + 64;                             // vrow, rankof
 }
 
-__device__ __forceinline__ float fmar(float x, float y, float z) { return fmaf(x, y, z); }
 __device__ __forceinline__ double fmar(double x, double y, double z) { return fma(x, y, z); }
 
 // Pair t of round `round` of the circle ordering on P columns (0 <= t < P/2,
@@ -117,14 +118,6 @@ __device__ __forceinline__ void jac_rotation(double al, double be, double ga, do
   *c = 1.0 / sqrt(fma(t, t, 1.0));
   *s = *c * t;
 }
-__device__ __forceinline__ void jac_rotation(float al, float be, float ga, float* c, float* s) {
-  const float zeta = (be - al) / (2.f * ga);
-  const float t = (zeta >= 0.f ? 1.f : -1.f) / (fabsf(zeta) + hypotf(1.f, zeta));
-  *c = 1.f / sqrtf(fmaf(t, t, 1.f));  // correctly rounded: no drift of the column norms
-  *s = *c * t;
-}
-__device__ __forceinline__ float sqrtr(float x) { return sqrtf(x); }
-__device__ __forceinline__ double sqrtr(double x) { return sqrt(x); }
 
 template <typename Real, bool kFinal>
 __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a) {
@@ -422,6 +415,183 @@ __global__ void __launch_bounds__(SVD_MAX_THREADS) jacobi_kernel(const JacArgs a
   }
 }
 
+// ---- Phase 1 by blocks ---------------------------------------------------
+// One-sided block Jacobi (the block-cyclic orderings of one-sided Jacobi,
+// e.g. Hari & Vesely; each block pair gets one inner sweep): the columns,
+// padded with zero columns, form nblk = 2 C blocks of w.  In each of the
+// nblk - 1 rounds of an outer sweep (circle ordering of the blocks) CTA k of
+// the cluster takes one pair of blocks, loads their 2w columns of B and V
+// (every row) from the work arrays into shared memory, runs one inner sweep
+// of one-sided Jacobi over them (2w - 1 rounds of w disjoint column pairs,
+// one warp per pair, one block barrier per round) and writes them back; a
+// cluster barrier (release / acquire) separates the outer rounds.  An outer
+// sweep visits every pair of columns in different blocks once, so a round of
+// the cluster does w times the work of one scalar round for one cluster
+// barrier instead of two.
+struct BlkArgs {
+  int b, w, nblk;   // columns, block width, blocks (twice the cluster size)
+  const double* B;  // input block (FP64), column-major
+  int64_t ldb;
+  float* Bw;        // work arrays: b rows x nblk w columns, ld b
+  float* Vw;
+  float* V32;       // output: V (b x b, ld b)
+  int max_sweeps;
+  float tol;        // rotate while |a_p.a_q| > tol |a_p| |a_q|
+  unsigned* info;   // outer sweeps taken
+};
+
+size_t blk_smem_bytes(int b, int w) { return (size_t)4 * w * b * sizeof(float); }
+constexpr int kRowsPerLane = SVD_MAX_B / 32;  // rows of a column per lane (b <= 256)
+constexpr int kLd = 8;                        // loads in flight per thread
+
+// Rotation of phase 1 (Rutishauser's formula) with the hardware's
+// approximate divide and reciprocal square root: phase 1 only preconditions
+// (its V is made orthogonal in FP64 afterwards and phase 2 restarts from
+// C = B V), so a rotation orthogonal to a few FP32 ulp is enough, and the
+// rotation is on the critical path of every inner round.  zeta^2 overflows
+// only where t is below FP32 resolution, and then t = 0.
+__device__ __forceinline__ void blk_rotation(float al, float be, float ga, float* c, float* s) {
+  const float zeta = __fdividef(be - al, 2.f * ga);
+  const float t = __fdividef(copysignf(1.f, zeta), fabsf(zeta) + __fsqrt_rn(fmaf(zeta, zeta, 1.f)));
+  *c = rsqrtf(fmaf(t, t, 1.f));
+  *s = *c * t;
+}
+
+__global__ void __launch_bounds__(SVD_MAX_THREADS) block_jacobi_f32_kernel(const BlkArgs a) {
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank(), ncl = (int)cl.num_blocks();
+  const int b = a.b, w = a.w, nblk = a.nblk, ncol = nblk * w;
+  const int tid = threadIdx.x, nth = blockDim.x, warp = tid >> 5, lane = tid & 31;
+  extern __shared__ float fsm[];
+  float* Bs = fsm;                      // local column l (0..2w-1), row i at Bs[l b + i]
+  float* Vs = Bs + (size_t)2 * w * b;
+  __shared__ int s_rot;
+  __shared__ double s_red[SVD_MAX_THREADS / 32];
+
+  // B 2^-e, e the exponent of max |B| (exact, inside the FP32 range)
+  double mx = 0.0;
+  for (int e = tid; e < b * b; e += nth)
+    mx = fmax(mx, fabs(a.B[(e % b) + (int64_t)(e / b) * a.ldb]));
+  mx = block_max(mx, s_red);
+  double scale = 1.0;
+  if (mx > 0.0) {
+    int ex = 0;
+    frexp(mx, &ex);
+    scale = ldexp(1.0, -ex);
+  }
+  // this CTA's share of the work arrays: columns rank, rank + C, ...
+  for (int j = rank; j < ncol; j += ncl)
+    for (int i = tid; i < b; i += nth) {
+      a.Bw[i + (int64_t)j * b] = (j < b) ? (float)(a.B[i + (int64_t)j * a.ldb] * scale) : 0.f;
+      a.Vw[i + (int64_t)j * b] = (i == j) ? 1.f : 0.f;
+    }
+  if (tid == 0) s_rot = 0;
+  cl.sync();
+
+  const float tol = a.tol;
+  int sweep = 0;
+  for (; sweep < a.max_sweeps; ++sweep) {
+    for (int round = 0; round < nblk - 1; ++round) {
+      int bp, bq;
+      rr_pair(round, rank, nblk, &bp, &bq);
+      // the two blocks are contiguous in the work arrays (ld b): batches of
+      // kLd loads in flight per thread before they are stored
+      for (int e0 = 0; e0 < 2 * w * b; e0 += kLd * nth) {
+        float xb[kLd], xv[kLd];
+#pragma unroll
+        for (int k = 0; k < kLd; ++k) {
+          const int e = e0 + k * nth + tid;
+          if (e < 2 * w * b) {
+            const int64_t g = (e < w * b) ? (int64_t)bp * w * b + e : (int64_t)bq * w * b + (e - w * b);
+            xb[k] = __ldcg(a.Bw + g);
+            xv[k] = __ldcg(a.Vw + g);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < kLd; ++k) {
+          const int e = e0 + k * nth + tid;
+          if (e < 2 * w * b) {
+            Bs[e] = xb[k];
+            Vs[e] = xv[k];
+          }
+        }
+      }
+      __syncthreads();
+      for (int ir = 0; ir < 2 * w - 1; ++ir) {
+        if (warp < w) {
+          int p, q;
+          rr_pair(ir, warp, 2 * w, &p, &q);
+          float* bpc = Bs + (size_t)p * b;
+          float* bqc = Bs + (size_t)q * b;
+          float sa = 0.f, sb = 0.f, sc = 0.f;
+#pragma unroll
+          for (int k = 0; k < kRowsPerLane; ++k) {
+            const int i = lane + 32 * k;
+            if (i < b) {
+              const float x = bpc[i], y = bqc[i];
+              sa = fmaf(x, x, sa);
+              sb = fmaf(y, y, sb);
+              sc = fmaf(x, y, sc);
+            }
+          }
+          for (int o = 16; o > 0; o >>= 1) {  // xor tree: the same sums in every lane
+            sa += __shfl_xor_sync(0xffffffffu, sa, o);
+            sb += __shfl_xor_sync(0xffffffffu, sb, o);
+            sc += __shfl_xor_sync(0xffffffffu, sc, o);
+          }
+          if (sc != 0.f && sc * sc > tol * tol * sa * sb) {
+            float c, s;
+            blk_rotation(sa, sb, sc, &c, &s);
+            if (lane == 0) s_rot = 1;
+            float* vpc = Vs + (size_t)p * b;
+            float* vqc = Vs + (size_t)q * b;
+            // every load before any store: the four columns' rows would
+            // otherwise be read one row at a time behind possibly aliasing stores
+            float x[kRowsPerLane], y[kRowsPerLane], u[kRowsPerLane], v[kRowsPerLane];
+#pragma unroll
+            for (int k = 0; k < kRowsPerLane; ++k) {
+              const int i = lane + 32 * k;
+              if (i < b) {
+                x[k] = bpc[i];
+                y[k] = bqc[i];
+                u[k] = vpc[i];
+                v[k] = vqc[i];
+              }
+            }
+#pragma unroll
+            for (int k = 0; k < kRowsPerLane; ++k) {
+              const int i = lane + 32 * k;
+              if (i < b) {
+                bpc[i] = fmaf(c, x[k], -s * y[k]);
+                bqc[i] = fmaf(s, x[k], c * y[k]);
+                vpc[i] = fmaf(c, u[k], -s * v[k]);
+                vqc[i] = fmaf(s, u[k], c * v[k]);
+              }
+            }
+          }
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < 2 * w * b; e += nth) {
+        const int l = e / b, i = e % b;
+        const int64_t gc = (l < w) ? (int64_t)bp * w + l : (int64_t)bq * w + (l - w);
+        a.Bw[i + gc * b] = Bs[e];
+        a.Vw[i + gc * b] = Vs[e];
+      }
+      cl.sync();  // the next round reads what this one wrote
+    }
+    // every CTA reads every flag: the same decision everywhere
+    int any = 0;
+    for (int k = 0; k < ncl; ++k) any |= *cl.map_shared_rank(&s_rot, k);
+    cl.sync();  // all flags read before any is reset
+    if (tid == 0) s_rot = 0;
+    if (!any) break;
+  }
+  if (rank == 0 && tid == 0 && a.info) a.info[0] = (unsigned)sweep;
+  for (int j = rank; j < b; j += ncl)
+    for (int i = tid; i < b; i += nth) a.V32[i + (int64_t)j * b] = __ldcg(a.Vw + i + (int64_t)j * b);
+}
+
 // Completes the columns of Us whose singular value is exactly zero: modified
 // Gram-Schmidt (twice) of unit vectors e_0, e_1, ... against the columns
 // already present, taking the first with a residual norm above 1/2.
@@ -532,19 +702,33 @@ int fp64_cluster() {
   return ncl;
 }
 
-// Cluster of the FP32 phase: the smallest one whose share of B and V fits in
-// shared memory, and at least kFp32MinCluster CTAs for blocks wider than 128
-// columns (each round's work then divides over more SMs; the side stream
-// reserves kSvdSms of them), capped at the size the FP64 phase can place.
-// At b = 256 on 16384^2 the FP32 phase took 934 ms over 64 launches with
-// clusters of 4, 759 ms with 8 and 679 ms with 16.
-constexpr int kFp32MinCluster = kSvdSms;
-int fp32_cluster(int b) {
-  const int hi = fp64_cluster();
-  const int lo = (b > 128) ? kFp32MinCluster : 1;
-  for (int c = lo; c < hi; c *= 2)
-    if (jac_smem_bytes<float>(b, c) <= 200 * 1024) return c;
-  return hi;
+// Phase 1 by blocks on a cluster of fp64_cluster() CTAs (16 where the device
+// places them): blocks of w = ceil(b / 2C) columns; the work arrays hold
+// b x 2C w floats each.
+int launch_block_jacobi(BlkArgs a, cudaStream_t st) {
+  const int ncl = fp64_cluster();
+  a.nblk = 2 * ncl;
+  a.w = (a.b + a.nblk - 1) / a.nblk;
+  const size_t smem = blk_smem_bytes(a.b, a.w);
+  RUTV_TRY(ensure_nonportable_cluster((const void*)block_jacobi_f32_kernel));
+  RUTV_TRY(ensure_smem((const void*)block_jacobi_f32_kernel, smem));
+  ProfScope prof(K_SVD32, 0.0, 8.0 * (double)a.b * a.b, st);
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = (unsigned)ncl;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3((unsigned)ncl);
+  cfg.blockDim = dim3((unsigned)(32 * (a.w > 4 ? a.w : 4)));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  RUTV_CK(cudaLaunchKernelEx(&cfg, block_jacobi_f32_kernel, a));
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
 }
 }  // namespace
 
@@ -574,16 +758,19 @@ int launch_small_svd(int b, const double* B, int64_t ldb, double* D, double* Us,
     float* V32 = (float*)s;
     double* H = (double*)(s + align256((size_t)b * b * sizeof(float)));
     double* Vb = (double*)((char*)H + align256((size_t)b * b * sizeof(double)));
-    // phase 1: FP32 sweeps down to the FP32 noise level
-    JacArgs a1 = {};
+    // phase 1: FP32 block sweeps down to the FP32 noise level; the work arrays
+    // borrow H and Vb (2 b^2 floats each, unused until phase 1 is done)
+    BlkArgs a1 = {};
     a1.b = b;
     a1.B = B;
     a1.ldb = ldb;
+    a1.Bw = (float*)H;
+    a1.Vw = (float*)Vb;
     a1.V32 = V32;
     a1.max_sweeps = 20;
-    a1.tol = 2.0 * (double)b * 0x1.0p-24;
+    a1.tol = (float)(2.0 * (double)b * 0x1.0p-24);
     a1.info = info ? info + 1 : nullptr;
-    RUTV_TRY((launch_jacobi<float, false>(a1, fp32_cluster(b), st)));
+    RUTV_TRY(launch_block_jacobi(a1, st));
     // two Newton-Schulz steps: V <- V H, H = 1.5 I - 0.5 V^T V (FP64)
     const int grid = (b * b + 255) / 256;
     svd_prep_kernel<<<grid, 256, 0, st>>>(b, V32, Vs, H);

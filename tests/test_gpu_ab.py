@@ -3,7 +3,9 @@
 The in-HBM executor and the out-of-HBM executor with its LRU block cache run
 the analyzer's task list; both are compared element by element with
 oracle.randutv_ab (U, T, V at 1e-12 relative on spectra whose singular
-values are separated), checked for the invariants of the factorization, and
+values are separated, or at 10x the oracle's own movement under a
+rounding-level perturbation of A where that floor is higher), checked for
+the invariants of the factorization, and
 the cache's I/O is checked against the analyzer's model of the dispatcher.
 """
 import pytest
@@ -31,6 +33,22 @@ def rel(x, y):
     return float((x - y).norm()) / (d if d > 0 else 1.0)
 
 
+def sensitivity(A, b, q, seed):
+    """How far the oracle's U, T, V move when A moves at rounding level (two
+    perturbations of size 1e-16 max|A|): the factorization fixes U and V only
+    to about eps ||A|| / gap, so a parity gate sits at 10x this floor where
+    the floor is above 1e-13."""
+    ref = oracle.randutv_ab(A, b, q, seed)
+    sens = {"U": 0.0, "T": 0.0, "V": 0.0}
+    for s in (5, 6):
+        g = torch.Generator().manual_seed(s)
+        Ap = A + torch.randn(A.shape, generator=g, dtype=f64) * 1e-16 * float(A.abs().max())
+        f = oracle.randutv_ab(Ap, b, q, seed)
+        for k in sens:
+            sens[k] = max(sens[k], rel(getattr(f, k), getattr(ref, k)))
+    return ref, {k: max(1e-12, 10.0 * v) for k, v in sens.items()}
+
+
 CASES = [("linear", 256, 256, 64, 1), ("linear", 300, 260, 64, 1), ("linear", 333, 517, 64, 2),
          ("linear", 517, 333, 128, 0), ("exp40", 200, 200, 32, 1), ("linear", 96, 80, 16, 1),
          ("gauss", 9, 1, 4, 0), ("gauss", 1, 7, 4, 1), ("linear", 64, 64, 64, 1)]
@@ -44,12 +62,13 @@ def test_ab_matches_oracle(pkg, kind, m, n, b, q, nstreams):
     torch.cuda.synchronize()
     assert pkg.randutv_stream_status() == 0
     U, T, V = U.cpu(), T.cpu(), V.cpu()
-    ref = oracle.randutv_ab(A, b, q, 7)
+    ref, gate = sensitivity(A, b, q, 7)
     assert oracle.recon_error(A, U, T, V) < 1e-13
     assert float(torch.tril(T, -1).abs().max()) == 0.0
-    assert rel(T, ref.T) < 1e-12
+    assert rel(T, ref.T) < gate["T"]
     if kind != "gauss":
-        assert rel(U, ref.U) < 1e-12 and rel(V, ref.V) < 1e-12
+        assert rel(U, ref.U) < gate["U"], (rel(U, ref.U), gate)
+        assert rel(V, ref.V) < gate["V"], (rel(V, ref.V), gate)
 
 
 def test_ab_is_deterministic_and_reports_nonfinite(pkg):
