@@ -13,59 +13,142 @@ namespace rutv {
 
 namespace {
 
-__device__ __forceinline__ void split3(double x, __nv_bfloat16* h0, __nv_bfloat16* h1,
-                                       __nv_bfloat16* h2) {
-  const __nv_bfloat16 a = __double2bfloat16(x);
-  const double r1 = x - (double)__bfloat162float(a);
-  const __nv_bfloat16 b = __double2bfloat16(r1);
-  const double r2 = r1 - (double)__bfloat162float(b);
-  *h0 = a;
-  *h1 = b;
-  *h2 = __double2bfloat16(r2);
+// FP32 split and join in FP32 arithmetic: x - bf16(x) and the next residual
+// are exact in FP32, and P0 + P1 spans at most 16 bits, so both give the same
+// bits as the FP64 forms (one rounding of an exact sum in the join).
+__device__ __forceinline__ void split3f(float x, __nv_bfloat16& h0, __nv_bfloat16& h1,
+                                        __nv_bfloat16& h2) {
+  h0 = __float2bfloat16_rn(x);
+  const float r1 = x - __bfloat162float(h0);
+  h1 = __float2bfloat16_rn(r1);
+  h2 = __float2bfloat16_rn(r1 - __bfloat162float(h1));
+}
+__device__ __forceinline__ void split3(double x, __nv_bfloat16& h0, __nv_bfloat16& h1,
+                                       __nv_bfloat16& h2) {
+  h0 = __double2bfloat16(x);
+  const double r1 = x - (double)__bfloat162float(h0);
+  h1 = __double2bfloat16(r1);
+  h2 = __double2bfloat16(r1 - (double)__bfloat162float(h1));
+}
+__device__ __forceinline__ void split3t(float x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  split3f(x, a, b, c);
+}
+__device__ __forceinline__ void split3t(double x, __nv_bfloat16& a, __nv_bfloat16& b, __nv_bfloat16& c) {
+  split3(x, a, b, c);
+}
+__device__ __forceinline__ float join3f(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c) {
+  return (__bfloat162float(a) + __bfloat162float(b)) + __bfloat162float(c);
+}
+__device__ __forceinline__ double join3d(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c) {
+  return (double)__bfloat162float(a) + (double)__bfloat162float(b) + (double)__bfloat162float(c);
+}
+template <typename T> __device__ __forceinline__ T join3t(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c);
+template <> __device__ __forceinline__ float join3t<float>(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c) {
+  return join3f(a, b, c);
+}
+template <> __device__ __forceinline__ double join3t<double>(__nv_bfloat16 a, __nv_bfloat16 b, __nv_bfloat16 c) {
+  return join3d(a, b, c);
 }
 
-__device__ __forceinline__ double join3(const __nv_bfloat16* P0, const __nv_bfloat16* P1,
-                                        const __nv_bfloat16* P2, int64_t o) {
-  return (double)__bfloat162float(P0[o]) + (double)__bfloat162float(P1[o]) +
-         (double)__bfloat162float(P2[o]);
-}
+// Tiles of 32 x 32 elements, 32 x 8 threads.  Without trans both sides are
+// read and written along columns; with trans the source tile goes through
+// shared memory so that both the read (along the source's columns) and the
+// write (along the planes' columns) are coalesced.
+constexpr int CT = 32, CR = 8;
 
 template <typename T>
-__global__ void split_kernel(const T* __restrict__ src, int64_t lds, int64_t rows, int64_t cols,
-                             int trans, __nv_bfloat16* P0, __nv_bfloat16* P1, __nv_bfloat16* P2,
-                             int64_t ldp) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
-    const double x = trans ? (double)src[j + i * lds] : (double)src[i + j * lds];
-    const int64_t o = i + j * ldp;
-    split3(x, P0 + o, P1 + o, P2 + o);
+__global__ void __launch_bounds__(CT * CR) split_kernel(const T* __restrict__ src, int64_t lds,
+                                                         int64_t rows, int64_t cols, int trans,
+                                                         __nv_bfloat16* P0, __nv_bfloat16* P1,
+                                                         __nv_bfloat16* P2, int64_t ldp) {
+  __shared__ T tile[CT][CT + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * CT, j0 = (int64_t)blockIdx.y * CT;  // dst tile
+  if (trans) {
+    // dst(i, j) = src(j, i) = src[j + i lds]: read src rows j0.. (contiguous) for columns i0..
+#pragma unroll
+    for (int k = 0; k < CT; k += CR) {
+      const int64_t sj = j0 + tx, si = i0 + ty + k;
+      if (sj < cols && si < rows) tile[ty + k][tx] = src[sj + si * lds];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < CT; k += CR) {
+      const int64_t i = i0 + tx, j = j0 + ty + k;
+      if (i < rows && j < cols) {
+        __nv_bfloat16 a, b, c;
+        split3t(tile[tx][ty + k], a, b, c);
+        const int64_t o = i + j * ldp;
+        P0[o] = a;
+        P1[o] = b;
+        P2[o] = c;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < CT; k += CR) {
+      const int64_t i = i0 + tx, j = j0 + ty + k;
+      if (i < rows && j < cols) {
+        __nv_bfloat16 a, b, c;
+        split3t(src[i + j * lds], a, b, c);
+        const int64_t o = i + j * ldp;
+        P0[o] = a;
+        P1[o] = b;
+        P2[o] = c;
+      }
+    }
   }
 }
 
 template <typename T>
-__global__ void merge_kernel(const __nv_bfloat16* P0, const __nv_bfloat16* P1,
-                             const __nv_bfloat16* P2, int64_t ldp, int64_t rows, int64_t cols,
-                             int trans, T* __restrict__ dst, int64_t ldd) {
-  const int64_t total = rows * cols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;  // element of dst
-    const int64_t o = trans ? (j + i * ldp) : (i + j * ldp);
-    dst[i + j * ldd] = (T)join3(P0, P1, P2, o);
+__global__ void __launch_bounds__(CT * CR) merge_kernel(const __nv_bfloat16* P0,
+                                                         const __nv_bfloat16* P1,
+                                                         const __nv_bfloat16* P2, int64_t ldp,
+                                                         int64_t rows, int64_t cols, int trans,
+                                                         T* __restrict__ dst, int64_t ldd) {
+  __shared__ T tile[CT][CT + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t i0 = (int64_t)blockIdx.x * CT, j0 = (int64_t)blockIdx.y * CT;  // dst tile
+  if (trans) {
+    // dst(i, j) = planes(j, i): read the planes' rows j0.. for their columns i0..
+#pragma unroll
+    for (int k = 0; k < CT; k += CR) {
+      const int64_t pj = j0 + tx, pi = i0 + ty + k;
+      if (pj < cols && pi < rows) {
+        const int64_t o = pj + pi * ldp;
+        tile[ty + k][tx] = join3t<T>(P0[o], P1[o], P2[o]);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < CT; k += CR) {
+      const int64_t i = i0 + tx, j = j0 + ty + k;
+      if (i < rows && j < cols) dst[i + j * ldd] = tile[tx][ty + k];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < CT; k += CR) {
+      const int64_t i = i0 + tx, j = j0 + ty + k;
+      if (i < rows && j < cols) {
+        const int64_t o = i + j * ldp;
+        dst[i + j * ldd] = join3t<T>(P0[o], P1[o], P2[o]);
+      }
+    }
   }
 }
 
+dim3 tile_grid(int64_t rows, int64_t cols) {
+  return dim3((unsigned)((rows + CT - 1) / CT), (unsigned)((cols + CT - 1) / CT));
+}
+
+// Columns by grid.y (striding), rows by grid.x x threads: no per-element division.
 __global__ void absmax_kernel(const float* __restrict__ src, int64_t lds, int64_t rows,
                               int64_t cols, unsigned* out) {
-  const int64_t total = rows * cols;
   float m = 0.f;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
-       e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = e % rows, j = e / rows;
-    m = fmaxf(m, fabsf(src[i + j * lds]));
-  }
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x)
+      m = fmaxf(m, fabsf(src[i + j * lds]));
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));  // m >= 0: bits order as values
 }
@@ -77,12 +160,23 @@ __global__ void scale_bf16_kernel(const float* __restrict__ src, int64_t lds, in
   const float mx = __uint_as_float(*amax);
   if (mx > 0.f && isfinite(mx)) frexpf(mx, &e);
   const float s = ldexpf(1.f, -e);  // exact power of two
-  const int64_t total = rows * cols;
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total;
-       t += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t i = t % rows, j = t / rows;
-    dst[i + j * ldd] = __float2bfloat16_rn(src[i + j * lds] * s);
-  }
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x)
+      dst[i + j * ldd] = __float2bfloat16_rn(src[i + j * lds] * s);
+}
+
+// grid of the two kernels above: enough CTAs of 256 threads for the rows of a
+// column, times up to the columns (at most 16 CTAs per SM in all)
+dim3 col_grid(int64_t rows, int64_t cols) {
+  int64_t bx = (rows + 255) / 256;
+  const int64_t cap = (int64_t)dev_info().sms * 16;
+  if (bx > cap) bx = cap;
+  int64_t by = cap / (bx > 0 ? bx : 1);
+  if (by > cols) by = cols;
+  if (by < 1) by = 1;
+  if (by > 65535) by = 65535;
+  return dim3((unsigned)(bx > 0 ? bx : 1), (unsigned)by);
 }
 
 __global__ void identity_planes_kernel(int64_t rows, int64_t cols, __nv_bfloat16* P0,
@@ -104,7 +198,7 @@ __global__ void diag_planes_kernel(__nv_bfloat16* P0, __nv_bfloat16* P1, __nv_bf
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = e % bi, j = e / bi, o = (k + i) + (k + j) * ld;
-    split3(i == j ? D[i] : 0.0, P0 + o, P1 + o, P2 + o);
+    split3(i == j ? D[i] : 0.0, P0[o], P1[o], P2[o]);
   }
 }
 
@@ -122,7 +216,7 @@ int split_f32(const float* src, int64_t lds, int64_t rows, int64_t cols, int tra
               const Planes& dst, int64_t r0, int64_t c0, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return 0;
   ProfScope prof(K_CONVERT, 0.0, 10.0 * rows * (double)cols, st);
-  split_kernel<float><<<grid_of(rows * cols), 256, 0, st>>>(
+  split_kernel<float><<<tile_grid(rows, cols), dim3(CT, CR), 0, st>>>(
       src, lds, rows, cols, trans, dst.at(0, r0, c0), dst.at(1, r0, c0), dst.at(2, r0, c0), dst.ld);
   note_launch();
   RUTV_CK(cudaGetLastError());
@@ -133,7 +227,7 @@ int split_f64(const double* src, int64_t lds, int64_t rows, int64_t cols, int tr
               const Planes& dst, int64_t r0, int64_t c0, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return 0;
   ProfScope prof(K_CONVERT, 0.0, 14.0 * rows * (double)cols, st);
-  split_kernel<double><<<grid_of(rows * cols), 256, 0, st>>>(
+  split_kernel<double><<<tile_grid(rows, cols), dim3(CT, CR), 0, st>>>(
       src, lds, rows, cols, trans, dst.at(0, r0, c0), dst.at(1, r0, c0), dst.at(2, r0, c0), dst.ld);
   note_launch();
   RUTV_CK(cudaGetLastError());
@@ -144,7 +238,7 @@ int merge_f32(const Planes& src, int64_t r0, int64_t c0, int64_t rows, int64_t c
               float* dst, int64_t ldd, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return 0;
   ProfScope prof(K_CONVERT, 0.0, 10.0 * rows * (double)cols, st);
-  merge_kernel<float><<<grid_of(rows * cols), 256, 0, st>>>(
+  merge_kernel<float><<<tile_grid(rows, cols), dim3(CT, CR), 0, st>>>(
       src.at(0, r0, c0), src.at(1, r0, c0), src.at(2, r0, c0), src.ld, rows, cols, trans, dst, ldd);
   note_launch();
   RUTV_CK(cudaGetLastError());
@@ -155,7 +249,7 @@ int merge_f64(const Planes& src, int64_t r0, int64_t c0, int64_t rows, int64_t c
               double* dst, int64_t ldd, cudaStream_t st) {
   if (rows <= 0 || cols <= 0) return 0;
   ProfScope prof(K_CONVERT, 0.0, 14.0 * rows * (double)cols, st);
-  merge_kernel<double><<<grid_of(rows * cols), 256, 0, st>>>(
+  merge_kernel<double><<<tile_grid(rows, cols), dim3(CT, CR), 0, st>>>(
       src.at(0, r0, c0), src.at(1, r0, c0), src.at(2, r0, c0), src.ld, rows, cols, trans, dst, ldd);
   note_launch();
   RUTV_CK(cudaGetLastError());
@@ -168,8 +262,8 @@ int scaled_bf16(const float* src, int64_t lds, int64_t rows, int64_t cols, __nv_
   ProfScope prof(K_CONVERT, 0.0, 10.0 * rows * (double)cols, st);
   unsigned* amax = (unsigned*)scratch;
   RUTV_CK(cudaMemsetAsync(amax, 0, sizeof(unsigned), st));
-  absmax_kernel<<<grid_of(rows * cols), 256, 0, st>>>(src, lds, rows, cols, amax);
-  scale_bf16_kernel<<<grid_of(rows * cols), 256, 0, st>>>(src, lds, rows, cols, amax, dst, ldd);
+  absmax_kernel<<<col_grid(rows, cols), 256, 0, st>>>(src, lds, rows, cols, amax);
+  scale_bf16_kernel<<<col_grid(rows, cols), 256, 0, st>>>(src, lds, rows, cols, amax, dst, ldd);
   note_launch(2);
   RUTV_CK(cudaGetLastError());
   return 0;
