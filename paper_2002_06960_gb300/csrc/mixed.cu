@@ -36,6 +36,16 @@ __global__ void f32_to_f64_kernel(const float* __restrict__ src, int64_t lds, in
   }
 }
 
+// P(i, j) -= D(i, j) for an FP64 P and an FP32 D (rows x cols), columns by grid.y.
+__global__ void sub_f32_from_f64_kernel(double* __restrict__ P, int64_t ldp,
+                                        const float* __restrict__ D, int64_t ldd, int64_t rows,
+                                        int64_t cols) {
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x)
+      P[i + j * ldp] -= (double)D[i + j * ldd];
+}
+
 // tau_j <- 2 / Gm(j, j) for the reflectors that are not the identity (tau_j = 0).
 __global__ void retau_kernel(int c, const double* __restrict__ Gm, int64_t ldg,
                              double* __restrict__ tau) {
@@ -110,6 +120,7 @@ BgemmOut out_planes(const Planes& P, int64_t r0, int64_t c0, float alpha) {
 struct MixedWork {
   Planes T, Ut, Vt;             // m x n, m x m (U^T), n x n (V^T)
   Planes W, WSt, Xp, Sp, Vs;     // small operands as planes
+  Planes Pp;                     // blocked panel QR: the second half of the panel as planes
   Planes UsAll;                 // U_s of every block step, b x (steps b), kept for the row folds
   __nv_bfloat16 *G, *Yb;        // BF16 sketch operands
   float *Y, *Z, *X, *tmp, *scal;
@@ -167,6 +178,7 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add(planes_bytes(b, big));      // WSt
   add(planes_bytes(b, big));      // Xp (X^T or Xv/Xl)
   add(planes_bytes(b, b));        // Sp (S^T)
+  add(planes_bytes(big, b));      // Pp
   add(planes_bytes(b, nsteps(m, n, b) * b));  // UsAll
   add(planes_bytes(b, b));        // Vs
   add((size_t)pad8(big) * b * 2); // G
@@ -199,6 +211,7 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.WSt = carve_planes(ar, b, big);
   w.Xp = carve_planes(ar, b, big);
   w.Sp = carve_planes(ar, b, b);
+  w.Pp = carve_planes(ar, big, b);
   w.UsAll = carve_planes(ar, b, nsteps(m, n, b) * b);
   w.Vs = carve_planes(ar, b, b);
   w.G = (__nv_bfloat16*)ar.take((size_t)pad8(big) * b * 2);
@@ -308,8 +321,10 @@ int mixed_round_w(MCtx& c, int64_t r, int64_t c0, int64_t nc) {
 // the Gram W~^T W~ (Gram64, ld bi) that mixed_wy needs.  Panels of more than
 // 128 columns are factored in two halves: the QR of the first h = 128
 // columns, whose rounded block reflector I - W~1 S1 W~1^T (S1 from the
-// Gram's leading block, tau~ = 2 / |w~|^2) is applied to the rest in FP64,
-// P2 <- (I - W~1 S1 W~1^T)^T P2, then the QR of P2 below row h.  The
+// Gram's leading block, tau~ = 2 / |w~|^2) is applied to the rest,
+// P2 <- (I - W~1 S1 W~1^T)^T P2 (its long products to FP32 accuracy on the
+// tensor cores, as every other update of the panel's source), then the QR of
+// P2 below row h in FP64.  The
 // reflectors are those of the unblocked factorization up to rounding; each
 // half keeps its rows in shared memory where the whole panel would not fit,
 // and its columns see at most 127 trailing columns.  The Gram is built by
@@ -336,13 +351,27 @@ int mixed_qr(MCtx& c, int64_t r, int64_t bi, double* P, int reserve) {
   note_launch();
   RUTV_CK(cudaGetLastError());
   RUTV_TRY(launch_wy_factor(h, w.Gram64, w.tau, w.S64, c.st, bi));
+  // P2 <- P2 - W~1 (S1^T (W~1^T P2)): the two long products on the tensor
+  // cores with the six-pair split (FP32-level, like every update of T), the
+  // h x h product by S1 in FP64
   double* P2 = P + h * r;
-  RUTV_TRY(launch_dgemm(true, false, h, h2, r, 1.0, w.W64, r, P2, r, 0.0, w.qrX, h, w.dgemm,
-                        w.dgemm_bytes, c.st));
+  RUTV_TRY(split_f64(P2, r, r, h2, 0, w.Pp, 0, 0, c.st));
+  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, h), opnd(w.Pp, 3, 0, 0, 0, r, h2), (int)h, (int)h2,
+                        (int)r, 3, out_f32(w.X, h), c.status, c.st, c.cap()));
+  RUTV_TRY(f32_to_f64(w.X, h, h, h2, w.qrX, h, c.st));
   RUTV_TRY(launch_dgemm(true, false, h, h2, h, 1.0, w.S64, h, w.qrX, h, 0.0, w.qrY, h, w.dgemm,
                         w.dgemm_bytes, c.st));
-  RUTV_TRY(launch_dgemm(false, false, r, h2, h, -1.0, w.W64, r, w.qrY, h, 1.0, P2, r, w.dgemm,
-                        w.dgemm_bytes, c.st));
+  RUTV_TRY(split_f64(w.qrY, h, h, h2, 0, w.Sp, 0, 0, c.st));
+  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 1, r, h), opnd(w.Sp, 3, 0, 0, 0, h, h2), (int)r, (int)h2,
+                        (int)h, 3, out_f32(w.tmp, r), c.status, c.st, c.cap()));
+  {
+    ProfScope prof(K_CONVERT, 0.0, 20.0 * (double)r * h2, c.st);
+    const int64_t bx = (r + 255) / 256;
+    sub_f32_from_f64_kernel<<<dim3((unsigned)(bx < 64 ? bx : 64), (unsigned)h2), 256, 0, c.st>>>(
+        P2, r, w.tmp, r, r, h2);
+    note_launch();
+    RUTV_CK(cudaGetLastError());
+  }
   RUTV_TRY(launch_householder_qr(r - h, h2, P2 + h, r, w.W2, w.tau + h, w.qr, c.status + 2,
                                  c.status, c.st, reserve));
   // W(:, h:) = [0; W2], rounded
