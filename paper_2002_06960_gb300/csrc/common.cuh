@@ -122,28 +122,27 @@ __device__ __forceinline__ bool grid_barrier(unsigned* bar, unsigned nblocks, un
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
+    // The error word is read only while waiting: a CTA that gives up never
+    // arrives, and the others see its error within 64 polls.  The acquiring
+    // poll (with the block barrier after it) orders what follows, so no fence
+    // is needed after it.
     int ok = 1;
-    if (ld_acquire_gpu(err) != 0) {
-      ok = 0;
-    } else {
-      const unsigned target = nblocks * (++epoch);
-      __threadfence();
-      red_release_add_gpu(bar, 1u);
-      if (ld_acquire_gpu(bar) < target) {
-        const unsigned long long t0 = globaltimer_ns();
-        unsigned spins = 0;
-        while (ld_acquire_gpu(bar) < target) {
-          if ((++spins & 63u) == 0) {
-            if (ld_acquire_gpu(err) != 0) { ok = 0; break; }
-            if (globaltimer_ns() - t0 > kWaitLimitNs) {
-              if (atomicCAS(err, 0u, (unsigned)RANDUTV_ETIMEOUT) == 0u) atomicExch(err + 1, site);
-              ok = 0;
-              break;
-            }
+    const unsigned target = nblocks * (++epoch);
+    __threadfence();
+    red_release_add_gpu(bar, 1u);
+    if (ld_acquire_gpu(bar) < target) {
+      const unsigned long long t0 = globaltimer_ns();
+      unsigned spins = 0;
+      while (ld_acquire_gpu(bar) < target) {
+        if ((++spins & 63u) == 0) {
+          if (ld_acquire_gpu(err) != 0) { ok = 0; break; }
+          if (globaltimer_ns() - t0 > kWaitLimitNs) {
+            if (atomicCAS(err, 0u, (unsigned)RANDUTV_ETIMEOUT) == 0u) atomicExch(err + 1, site);
+            ok = 0;
+            break;
           }
         }
       }
-      __threadfence();
     }
     s_ok = ok;
   }

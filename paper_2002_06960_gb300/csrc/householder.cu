@@ -34,12 +34,18 @@ constexpr int QR_THREADS = 256;
 constexpr int QR_WARPS = QR_THREADS / 32;
 constexpr size_t kQrSmemMax = 216 * 1024;  // own rows kept in shared memory up to this size
 constexpr int kOwnMax = 37;  // owned columns per warp: ceil(255 / 7) with one CTA, c <= 256
+constexpr int kQrMaxCols = 256;   // panel columns
+constexpr int kLoadsPerLane = 8;  // partials per lane: CTAs <= 256
 
-struct QrArgs {
+// Real: element type of the panel and of its per-element arithmetic (double,
+// or float for the mixed-precision form); the cross-CTA partials, tau and
+// the reflector scalars are FP64 in both.
+template <typename Real>
+struct QrArgsT {
   int64_t r, c;
-  double* A;
+  Real* A;
   int64_t lda;
-  double* W;       // r x c, ld r
+  Real* W;         // r x c, ld r
   double* tau;     // c
   double* part1;   // nblocks: partial squared norms below the diagonal
   double* part2;   // nblocks x c: partial dot products
@@ -48,24 +54,32 @@ struct QrArgs {
   unsigned* bar;   // {count, generation}
   unsigned* err;
 };
+using QrArgs = QrArgsT<double>;
 
-template <bool kSmem>
-__global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a) {
-  extern __shared__ double smA[];  // kSmem: own rows, column-major, ld rows_per
+template <typename Real, bool kSmem>
+__global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgsT<Real> a) {
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  // kSmem: own rows, column-major with an odd leading dimension ldr (so that
+  // a warp's threads, one per column, hit distinct banks), then one column
+  // more for the reflector v over own rows
+  Real* smA = reinterpret_cast<Real*>(qr_smem);
   __shared__ double red[QR_WARPS];
   __shared__ double s_coef[4];  // tau, scale, beta
   // owned columns' (sum of partials, A(j, l)) per warp 1..: at most
   // ceil((c - 1) / ((QR_WARPS - 1) nb)) each (checked on the host)
   __shared__ double s_own[QR_WARPS - 1][kOwnMax][2];
+  __shared__ double s_tot[kQrMaxCols];  // tau (v . A(:, l)) of column j's trailing columns
   const unsigned nb = gridDim.x;
   const int64_t rows_per = (a.r + nb - 1) / nb;
   const int64_t i0 = (int64_t)blockIdx.x * rows_per;
   const int64_t i1 = (i0 + rows_per < a.r) ? i0 + rows_per : a.r;
+  const int64_t nr = (i1 > i0) ? i1 - i0 : 0;
+  const int64_t ldr = rows_per | 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned epoch = 0;  // grid barriers passed (thread 0)
   // element (i, l) of the panel, i in [i0, i1)
-  auto at = [&](int64_t i, int64_t l) -> double& {
-    if (kSmem) return smA[(i - i0) + l * rows_per];
+  auto at = [&](int64_t i, int64_t l) -> Real& {
+    if (kSmem) return smA[(i - i0) + l * ldr];
     return a.A[i + l * a.lda];
   };
   if (kSmem) {
@@ -82,39 +96,61 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
     // v . A(j:r, l) = A(j, l) + (x . A(j+1:r, l)) / (alpha - beta), so these
     // partials and the row A(j, j:c) are all the exchange the column needs.
     const int64_t lo = (i0 > j + 1) ? i0 : j + 1;
-    double ss = 0.0;
-    for (int64_t i = lo + threadIdx.x; i < i1; i += QR_THREADS) {
-      const double x = at(i, j);
-      ss = fma(x, x, ss);
-    }
-    // Each warp takes its columns l = j+1+warp+QR_WARPS*t in groups of 8 and
-    // walks its rows once per group, so the loads of a row are independent
-    // and in flight together.
-    for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
-      double d[8];
+    if constexpr (kSmem) {
+      // thread t < c takes column t: x . A(own rows, t), and |x|^2 for t = j,
+      // each a fixed-order sum of its own (no cross-lane reduction)
+      const int t = threadIdx.x;
+      if (t >= j && t < a.c) {
+        const Real* __restrict__ xj = smA + j * ldr;
+        const Real* __restrict__ xt = smA + (int64_t)t * ldr;
+        Real d0 = 0, d1 = 0;
+        int64_t lr = lo - i0;
+        for (; lr + 1 < nr; lr += 2) {
+          d0 = fma(xj[lr], xt[lr], d0);
+          d1 = fma(xj[lr + 1], xt[lr + 1], d1);
+        }
+        if (lr < nr) d0 = fma(xj[lr], xt[lr], d0);
+        const double d = (double)(d0 + d1);
+        if (t == j) a.part1[blockIdx.x] = d;
+        else a.part2[(int64_t)blockIdx.x * a.c + t] = d;
+      }
+      if (j >= i0 && j < i1)
+        for (int64_t l = j + t; l < a.c; l += QR_THREADS) a.rowj[l] = (double)at(j, l);
+    } else {
+      Real ss = 0;
+      for (int64_t i = lo + threadIdx.x; i < i1; i += QR_THREADS) {
+        const Real x = at(i, j);
+        ss = fma(x, x, ss);
+      }
+      // Each warp takes its columns l = j+1+warp+QR_WARPS*t in groups of 8 and
+      // walks its rows once per group, so the loads of a row are independent
+      // and in flight together.
+      for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
+        Real d[8];
 #pragma unroll
-      for (int t = 0; t < 8; ++t) d[t] = 0.0;
-      for (int64_t i = lo + lane; i < i1; i += 32) {
-        const double x = at(i, j);
+        for (int t = 0; t < 8; ++t) d[t] = 0;
+        for (int64_t i = lo + lane; i < i1; i += 32) {
+          const Real x = at(i, j);
+#pragma unroll
+          for (int t = 0; t < 8; ++t) {
+            const int64_t l = l0 + (int64_t)t * QR_WARPS;
+            if (l < a.c) d[t] = fma(x, at(i, l), d[t]);
+          }
+        }
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
+          double y = (double)d[t];
+          for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
           const int64_t l = l0 + (int64_t)t * QR_WARPS;
-          if (l < a.c) d[t] = fma(x, at(i, l), d[t]);
+          if (lane == 0 && l < a.c) a.part2[(int64_t)blockIdx.x * a.c + l] = y;
         }
       }
-#pragma unroll
-      for (int t = 0; t < 8; ++t) {
-        double y = d[t];
-        for (int o = 16; o > 0; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
-        const int64_t l = l0 + (int64_t)t * QR_WARPS;
-        if (lane == 0 && l < a.c) a.part2[(int64_t)blockIdx.x * a.c + l] = y;
-      }
+      // the CTA that owns row j publishes it
+      if (j >= i0 && j < i1)
+        for (int64_t l = j + threadIdx.x; l < a.c; l += QR_THREADS) a.rowj[l] = (double)at(j, l);
+      const double ssum = block_sum((double)ss, red);
+      if (threadIdx.x == 0) a.part1[blockIdx.x] = ssum;
     }
-    // the CTA that owns row j publishes it
-    if (j >= i0 && j < i1)
-      for (int64_t l = j + threadIdx.x; l < a.c; l += QR_THREADS) a.rowj[l] = at(j, l);
-    ss = block_sum(ss, red);
-    if (threadIdx.x == 0) a.part1[blockIdx.x] = ss;
     if (!grid_barrier(a.bar, nb, a.err, 1, epoch)) return;
 
     // ---- (2) reflector scalars (every CTA, same order), and the sums of the
@@ -122,13 +158,21 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
     // reduces |x|^2 while warps 1.. load and sum the owned columns' partials
     // (they do not depend on the reflector), so the two L2 round trips overlap.
     if (warp == 0) {
-      // lanes load the partials in parallel; the fixed shuffle tree makes the
-      // sum identical in every CTA
+      // lanes load the partials in parallel, all in flight at once, and add
+      // them in a fixed order; the fixed shuffle tree makes the sum identical
+      // in every CTA
+      double v[kLoadsPerLane];
+#pragma unroll
+      for (int q = 0; q < kLoadsPerLane; ++q) {
+        const unsigned t = lane + 32u * q;
+        v[q] = (t < nb) ? __ldcg(a.part1 + t) : 0.0;
+      }
+      const double alpha = __ldcg(a.rowj + j);
       double sig2 = 0.0;
-      for (unsigned t = lane; t < nb; t += 32) sig2 += __ldcg(a.part1 + t);
+#pragma unroll
+      for (int q = 0; q < kLoadsPerLane; ++q) sig2 += v[q];
       for (int o = 16; o > 0; o >>= 1) sig2 += __shfl_xor_sync(0xffffffffu, sig2, o);
       if (lane == 0) {
-        const double alpha = __ldcg(a.rowj + j);
         double tau, scale, beta;
         if (sig2 == 0.0) {
           tau = 0.0; beta = alpha; scale = 0.0;
@@ -145,8 +189,15 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
       int t = 0;
       for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * (warp - 1); l < a.c;
            l += (int64_t)nb * (QR_WARPS - 1), ++t) {
+        double v[kLoadsPerLane];
+#pragma unroll
+        for (int q = 0; q < kLoadsPerLane; ++q) {
+          const unsigned u = lane + 32u * q;
+          v[q] = (u < nb) ? __ldcg(a.part2 + (int64_t)u * a.c + l) : 0.0;
+        }
         double sp = 0.0;
-        for (unsigned u = lane; u < nb; u += 32) sp += __ldcg(a.part2 + (int64_t)u * a.c + l);
+#pragma unroll
+        for (int q = 0; q < kLoadsPerLane; ++q) sp += v[q];
         for (int o = 16; o > 0; o >>= 1) sp += __shfl_xor_sync(0xffffffffu, sp, o);
         if (lane == 0) {
           s_own[warp - 1][t][0] = sp;
@@ -156,6 +207,7 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
     }
     __syncthreads();
     const double tau = s_coef[0], scale = s_coef[1];
+    const Real scale_r = (Real)scale;
     if (warp > 0 && lane == 0) {
       int t = 0;
       for (int64_t l = j + 1 + blockIdx.x + (int64_t)nb * (warp - 1); l < a.c;
@@ -164,35 +216,57 @@ __global__ void __launch_bounds__(QR_THREADS) householder_panel_kernel(QrArgs a)
     }
     if (!grid_barrier(a.bar, nb, a.err, 2, epoch)) return;
 
-    // ---- (3) rank-1 update of own rows, write W(:, j), R(j, j), zeros
+    // ---- (3) rank-1 update of own rows, write W(:, j), R(j, j), zeros; the
+    // published tau (v . A(:, l)) come into shared memory in one round trip
     const int64_t lo3 = (i0 > j) ? i0 : j;
-    if (tau != 0.0) {
-      for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
-        double w[8];
-#pragma unroll
-        for (int t = 0; t < 8; ++t) {
-          const int64_t l = l0 + (int64_t)t * QR_WARPS;
-          w[t] = (l < a.c) ? __ldcg(a.tot + l) : 0.0;
+    if constexpr (kSmem) {
+      // v over own rows into shared memory, then thread t > j updates column t
+      if (tau != 0.0) {
+        const int t = threadIdx.x;
+        Real w = 0;
+        if (t > j && t < a.c) w = (Real)__ldcg(a.tot + t);
+        Real* __restrict__ sv = smA + a.c * ldr;
+        for (int64_t lr = lo3 - i0 + t; lr < nr; lr += QR_THREADS)
+          sv[lr] = (i0 + lr == j) ? (Real)1 : smA[lr + j * ldr] * scale_r;
+        __syncthreads();
+        if (t > j && t < a.c) {
+          Real* __restrict__ xt = smA + (int64_t)t * ldr;
+          const Real* __restrict__ svc = sv;
+#pragma unroll 4
+          for (int64_t lr = lo3 - i0; lr < nr; ++lr) xt[lr] = fma(-svc[lr], w, xt[lr]);
         }
-        for (int64_t i = lo3 + lane; i < i1; i += 32) {
-          const double v = (i == j) ? 1.0 : at(i, j) * scale;
+      }
+    } else {
+      if (tau != 0.0) {
+        for (int64_t l = j + 1 + threadIdx.x; l < a.c; l += QR_THREADS) s_tot[l] = __ldcg(a.tot + l);
+        __syncthreads();
+        for (int64_t l0 = j + 1 + warp; l0 < a.c; l0 += 8 * (int64_t)QR_WARPS) {
+          Real w[8];
 #pragma unroll
           for (int t = 0; t < 8; ++t) {
             const int64_t l = l0 + (int64_t)t * QR_WARPS;
-            if (l < a.c) at(i, l) = fma(-v, w[t], at(i, l));
+            w[t] = (l < a.c) ? (Real)s_tot[l] : (Real)0;
+          }
+          for (int64_t i = lo3 + lane; i < i1; i += 32) {
+            const Real v = (i == j) ? (Real)1 : at(i, j) * scale_r;
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+              const int64_t l = l0 + (int64_t)t * QR_WARPS;
+              if (l < a.c) at(i, l) = fma(-v, w[t], at(i, l));
+            }
           }
         }
       }
     }
     __syncthreads();  // the updates above read A(:, j); rewrite it only now
     for (int64_t i = i0 + threadIdx.x; i < i1; i += QR_THREADS) {
-      double wv;
-      if (i < j) wv = 0.0;
-      else if (i == j) wv = 1.0;
-      else wv = (tau != 0.0) ? at(i, j) * scale : 0.0;
+      Real wv;
+      if (i < j) wv = 0;
+      else if (i == j) wv = 1;
+      else wv = (tau != 0.0) ? at(i, j) * scale_r : (Real)0;
       a.W[i + j * a.r] = wv;
-      if (i > j) at(i, j) = 0.0;
-      if (i == j) at(i, j) = s_coef[2];
+      if (i > j) at(i, j) = 0;
+      if (i == j) at(i, j) = (Real)s_coef[2];
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) a.tau[j] = tau;
     __syncthreads();
@@ -217,25 +291,30 @@ int qr_blocks(int64_t r, int reserve_sms = 0) {
 }
 
 // Scratch layout: part1 (SMs + 1), part2 (SMs x c), tot (c), rowj (c), in doubles.
-void qr_carve(QrArgs& a, double* base, int sms) {
+template <typename Real>
+void qr_carve(QrArgsT<Real>& a, double* base, int sms) {
   a.part1 = base;
   a.part2 = a.part1 + sms + 1;
   a.tot = a.part2 + (size_t)sms * a.c;
   a.rowj = a.tot + a.c;
 }
 
-int qr_launch(QrArgs& a, int nb, cudaStream_t st) {
-  if (a.c - 1 > (int64_t)(QR_WARPS - 1) * nb * kOwnMax) return RANDUTV_EUNSUPPORTED;
+template <typename Real>
+int qr_launch(QrArgsT<Real>& a, int nb, cudaStream_t st) {
+  if (a.c > kQrMaxCols || nb > 32 * kLoadsPerLane ||
+      a.c - 1 > (int64_t)(QR_WARPS - 1) * nb * kOwnMax)
+    return RANDUTV_EUNSUPPORTED;
   const int64_t rows_per = (a.r + nb - 1) / nb;
-  const size_t smem = (size_t)rows_per * (size_t)a.c * sizeof(double);
+  // own rows (leading dimension rows_per | 1) and the reflector column
+  const size_t smem = (size_t)(rows_per | 1) * (size_t)(a.c + 1) * sizeof(Real);
   void* args[] = {&a};
   if (smem <= kQrSmemMax) {
-    RUTV_TRY(ensure_smem((const void*)householder_panel_kernel<true>, kQrSmemMax));
-    RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel<true>, dim3(nb),
-                                        dim3(QR_THREADS), args, smem, st));
+    const void* fn = (const void*)householder_panel_kernel<Real, true>;
+    RUTV_TRY(ensure_smem(fn, kQrSmemMax));
+    RUTV_CK(cudaLaunchCooperativeKernel(fn, dim3(nb), dim3(QR_THREADS), args, smem, st));
   } else {
-    RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel<false>, dim3(nb),
-                                        dim3(QR_THREADS), args, 0, st));
+    RUTV_CK(cudaLaunchCooperativeKernel((const void*)householder_panel_kernel<Real, false>,
+                                        dim3(nb), dim3(QR_THREADS), args, 0, st));
   }
   note_launch();
   return 0;
@@ -311,6 +390,20 @@ int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* 
   qr_carve(a, (double*)scratch, dev_info().sms);
   a.bar = bar; a.err = err;
   ProfScope prof(K_QR, 2.0 * (double)c * c * ((double)r - c / 3.0), 24.0 * (double)r * c, st);
+  RUTV_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
+  return qr_launch(a, nb, st);
+}
+
+int launch_householder_qr_f32(int64_t r, int64_t c, float* A, int64_t lda, float* W, double* tau,
+                              char* scratch, unsigned* bar, unsigned* err, cudaStream_t st,
+                              int reserve_sms) {
+  if (c <= 0) return 0;
+  const int nb = qr_blocks(r, reserve_sms);
+  QrArgsT<float> a;
+  a.r = r; a.c = c; a.A = A; a.lda = lda; a.W = W; a.tau = tau;
+  qr_carve(a, (double*)scratch, dev_info().sms);
+  a.bar = bar; a.err = err;
+  ProfScope prof(K_QR, 2.0 * (double)c * c * ((double)r - c / 3.0), 12.0 * (double)r * c, st);
   RUTV_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
   return qr_launch(a, nb, st);
 }
