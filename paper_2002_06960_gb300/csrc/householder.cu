@@ -37,9 +37,9 @@ constexpr int kOwnMax = 37;  // owned columns per warp: ceil(255 / 7) with one C
 constexpr int kQrMaxCols = 256;   // panel columns
 constexpr int kLoadsPerLane = 8;  // partials per lane: CTAs <= 256
 
-// Real: element type of the panel and of its per-element arithmetic (double,
-// or float for the mixed-precision form); the cross-CTA partials, tau and
-// the reflector scalars are FP64 in both.
+// Real: element type of the panel and of its per-element arithmetic (the
+// library instantiates double); the cross-CTA partials, tau and the
+// reflector scalars are FP64.
 template <typename Real>
 struct QrArgsT {
   int64_t r, c;
@@ -331,7 +331,7 @@ int qr_launch(QrArgsT<Real>& a, int nb, cudaStream_t st) {
 // Gm(l, i) (Gm is symmetric) so that the lanes read contiguous memory, and
 // the next row's operands are loaded while the current row is reduced.  Only
 // the strictly lower part of Gm is read (the diagonal enters through tau).
-constexpr int WY_WARPS = 8;
+constexpr int WY_WARPS = 1;   // one column per CTA: the FP64 work spreads over the SMs
 constexpr int WY_MAXC = 256;
 
 __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const double* __restrict__ Gm,
@@ -340,8 +340,9 @@ __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const d
                                                                    double* __restrict__ S) {
   __shared__ double col[WY_WARPS][WY_MAXC];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int k = blockIdx.x * WY_WARPS + warp;
-  if (k >= c) return;  // whole warps leave; no block barrier below
+  // the longest columns (largest k) are launched first
+  const int k = c - 1 - (int)(blockIdx.x * WY_WARPS + warp);
+  if (k < 0) return;  // whole warps leave; no block barrier below
   double* sk = col[warp];
   constexpr int NL = WY_MAXC / 32;  // operands per lane per row
   double gcur[NL], gnext[NL];
@@ -358,11 +359,16 @@ __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const d
   for (int i = k; i >= 0; --i) {
     load_row(i - 1, gnext);
     const double tnext = (i > 0) ? tau[i - 1] : 0.0;
+    // groups t with a live operand (l = i+1+32t <= k): warp-uniform, so the
+    // FMA slots past the column's end are skipped rather than predicated
+    const int nt = (k - i + 31) >> 5;
     double acc = 0.0;
 #pragma unroll
     for (int t = 0; t < NL; ++t) {
-      const int l = i + 1 + lane + 32 * t;
-      if (l <= k) acc = fma(gcur[t], sk[l], acc);
+      if (t < nt) {
+        const int l = i + 1 + lane + 32 * t;
+        if (l <= k) acc = fma(gcur[t], sk[l], acc);
+      }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) sk[i] = tcur * (((i == k) ? 1.0 : 0.0) - acc);
@@ -390,20 +396,6 @@ int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* 
   qr_carve(a, (double*)scratch, dev_info().sms);
   a.bar = bar; a.err = err;
   ProfScope prof(K_QR, 2.0 * (double)c * c * ((double)r - c / 3.0), 24.0 * (double)r * c, st);
-  RUTV_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
-  return qr_launch(a, nb, st);
-}
-
-int launch_householder_qr_f32(int64_t r, int64_t c, float* A, int64_t lda, float* W, double* tau,
-                              char* scratch, unsigned* bar, unsigned* err, cudaStream_t st,
-                              int reserve_sms) {
-  if (c <= 0) return 0;
-  const int nb = qr_blocks(r, reserve_sms);
-  QrArgsT<float> a;
-  a.r = r; a.c = c; a.A = A; a.lda = lda; a.W = W; a.tau = tau;
-  qr_carve(a, (double*)scratch, dev_info().sms);
-  a.bar = bar; a.err = err;
-  ProfScope prof(K_QR, 2.0 * (double)c * c * ((double)r - c / 3.0), 12.0 * (double)r * c, st);
   RUTV_CK(cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), st));
   return qr_launch(a, nb, st);
 }

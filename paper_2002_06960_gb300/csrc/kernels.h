@@ -33,11 +33,6 @@ int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* 
                           int reserve_sms = 0);
 // S (c x c, ld c) from the Gram matrix of the reflectors (its diagonal and
 // strictly lower part are read, leading dimension ldg; 0 means c) and tau.
-// The same QR in FP32 (panel, reflectors and per-element arithmetic; tau and
-// the reductions across CTAs in FP64), for the mixed-precision form.
-int launch_householder_qr_f32(int64_t r, int64_t c, float* A, int64_t lda, float* W, double* tau,
-                              char* scratch, unsigned* bar, unsigned* err, cudaStream_t st,
-                              int reserve_sms = 0);
 int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st,
                      int64_t ldg = 0);
 

@@ -26,6 +26,26 @@ namespace rutv {
 
 namespace {
 
+__global__ void f32_to_f64_kernel(const float* __restrict__ src, int64_t lds, int64_t rows,
+                                  int64_t cols, double* __restrict__ dst, int64_t ldd) {
+  const int64_t total = rows * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % rows, j = e / rows;
+    dst[i + j * ldd] = (double)src[i + j * lds];
+  }
+}
+
+// P(i, j) -= D(i, j) for an FP64 P and an FP32 D (rows x cols), columns by grid.y.
+__global__ void sub_f32_from_f64_kernel(double* __restrict__ P, int64_t ldp,
+                                        const float* __restrict__ D, int64_t ldd, int64_t rows,
+                                        int64_t cols) {
+  for (int64_t j = blockIdx.y; j < cols; j += gridDim.y)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < rows;
+         i += (int64_t)gridDim.x * blockDim.x)
+      P[i + j * ldp] -= (double)D[i + j * ldd];
+}
+
 // tau_j <- 2 / Gm(j, j) for the reflectors that are not the identity (tau_j = 0).
 __global__ void retau_kernel(int c, const double* __restrict__ Gm, int64_t ldg,
                              double* __restrict__ tau) {
@@ -39,6 +59,15 @@ int grid_of(int64_t total) {
   if (blocks > cap) blocks = cap;
   if (blocks < 1) blocks = 1;
   return (int)blocks;
+}
+
+int f32_to_f64(const float* src, int64_t lds, int64_t rows, int64_t cols, double* dst, int64_t ldd,
+               cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return 0;
+  f32_to_f64_kernel<<<grid_of(rows * cols), 256, 0, st>>>(src, lds, rows, cols, dst, ldd);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
 }
 
 // Operand from planes; rows x cols is the extent of the valid source (a
@@ -91,10 +120,13 @@ BgemmOut out_planes(const Planes& P, int64_t r0, int64_t c0, float alpha) {
 struct MixedWork {
   Planes T, Ut, Vt;             // m x n, m x m (U^T), n x n (V^T)
   Planes W, WSt, Xp, Sp, Vs;     // small operands as planes
+  Planes Pp;                     // blocked panel QR: the second half of the panel as planes
   Planes UsAll;                 // U_s of every block step, b x (steps b), kept for the row folds
   __nv_bfloat16 *G, *Yb;        // BF16 sketch operands
   float *Y, *Z, *X, *tmp, *scal;
-  double *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64;
+  double *Y64, *W64, *tau, *Gram64, *S64, *D, *Us64, *Vs64, *blk64;
+  double* W2;        // blocked panel QR: reflectors of the second half (ld r - h)
+  double *qrX, *qrY; // blocked panel QR: W1^T P2 and S1^T W1^T P2
   char* qr;
   char* svd;
   double* dgemm;
@@ -146,13 +178,15 @@ size_t mixed_bytes(int64_t m, int64_t n, int64_t b) {
   add(planes_bytes(b, big));      // WSt
   add(planes_bytes(b, big));      // Xp (X^T or Xv/Xl)
   add(planes_bytes(b, b));        // Sp (S^T)
+  add(planes_bytes(big, b));      // Pp
   add(planes_bytes(b, nsteps(m, n, b) * b));  // UsAll
   add(planes_bytes(b, b));        // Vs
   add((size_t)pad8(big) * b * 2); // G
   add((size_t)pad8(big) * b * 2); // Yb
   for (int i = 0; i < 4; ++i) add((size_t)big * b * 4);  // Y, Z, X, tmp
   add(256);                       // scal
-  add((size_t)big * b * 8);       // W64
+  for (int i = 0; i < 3; ++i) add((size_t)big * b * 8);  // Y64, W64, W2
+  for (int i = 0; i < 2; ++i) add((size_t)b * b * 8);    // qrX, qrY
   add((size_t)b * 8 * 2);         // tau, D
   for (int i = 0; i < 5; ++i) add((size_t)b * b * 8);    // Gram64, S64, Us64, Vs64, blk64
   add(householder_scratch_bytes(b));
@@ -177,6 +211,7 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.WSt = carve_planes(ar, b, big);
   w.Xp = carve_planes(ar, b, big);
   w.Sp = carve_planes(ar, b, b);
+  w.Pp = carve_planes(ar, big, b);
   w.UsAll = carve_planes(ar, b, nsteps(m, n, b) * b);
   w.Vs = carve_planes(ar, b, b);
   w.G = (__nv_bfloat16*)ar.take((size_t)pad8(big) * b * 2);
@@ -186,7 +221,11 @@ MixedWork carve_mixed(Arena& ar, int64_t m, int64_t n, int64_t b) {
   w.X = (float*)ar.take((size_t)big * b * 4);
   w.tmp = (float*)ar.take((size_t)big * b * 4);
   w.scal = (float*)ar.take(256);
+  w.Y64 = (double*)ar.take((size_t)big * b * 8);
   w.W64 = (double*)ar.take((size_t)big * b * 8);
+  w.W2 = (double*)ar.take((size_t)big * b * 8);
+  w.qrX = (double*)ar.take((size_t)b * b * 8);
+  w.qrY = (double*)ar.take((size_t)b * b * 8);
   w.tau = (double*)ar.take((size_t)b * 8);
   w.D = (double*)ar.take((size_t)b * 8);
   w.Gram64 = (double*)ar.take((size_t)b * b * 8);
@@ -269,23 +308,83 @@ int mixed_apply_transposed(MCtx& c, const Planes& Xt, int64_t k, int64_t r, int6
   return 0;
 }
 
-// Householder QR of the panel P (r x bi, ld r, FP32, overwritten by R and
-// exact zeros) in FP32, its reflectors rounded to planes (W), kept in FP64
-// as W~ (W64), and the lower triangle of the FP64 Gram W~^T W~ (Gram64, ld
-// bi) that mixed_wy needs.  The panel is FP32-level data (the sketch, or a
-// block column of T's planes), so the QR loses nothing to FP32 arithmetic:
-// orthogonality comes from S, which is built in FP64 from the rounded
-// reflectors themselves.  In FP32 a panel of 256 columns keeps its rows in
-// shared memory up to about 32 x 10^3 rows, so it is factored in one pass.
-int mixed_qr(MCtx& c, int64_t r, int64_t bi, float* P, int reserve) {
+// Rounds the reflectors W64(:, c0:c0+nc) to their planes (columns c0: of W)
+// and writes the rounded values back, so that W64 holds W~ from here on.
+int mixed_round_w(MCtx& c, int64_t r, int64_t c0, int64_t nc) {
   MixedWork& w = c.w;
-  float* W32 = w.tmp;  // free until mixed_wy forms W S^T
-  RUTV_TRY(launch_householder_qr_f32(r, bi, P, r, W32, w.tau, w.qr, c.status + 2, c.status, c.st,
-                                     reserve));
-  RUTV_TRY(split_f32(W32, r, r, bi, 0, w.W, 0, 0, c.st));
-  RUTV_TRY(merge_f64(w.W, 0, 0, r, bi, 0, w.W64, r, c.st));
-  return launch_dgemm(true, false, bi, bi, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, bi, w.dgemm,
-                      w.dgemm_bytes, c.st, true);
+  RUTV_TRY(split_f64(w.W64 + c0 * r, r, r, nc, 0, w.W, 0, c0, c.st));
+  return merge_f64(w.W, 0, c0, r, nc, 0, w.W64 + c0 * r, r, c.st);
+}
+
+// Householder QR (FP64) of the panel P (r x bi, ld r) into the rounded
+// reflectors W~ (W64, ld r, and the planes W), tau, and the lower triangle of
+// the Gram W~^T W~ (Gram64, ld bi) that mixed_wy needs.  Panels of more than
+// 128 columns are factored in two halves: the QR of the first h = 128
+// columns, whose rounded block reflector I - W~1 S1 W~1^T (S1 from the
+// Gram's leading block, tau~ = 2 / |w~|^2) is applied to the rest,
+// P2 <- (I - W~1 S1 W~1^T)^T P2 (its long products to FP32 accuracy on the
+// tensor cores, as every other update of the panel's source), then the QR of
+// P2 below row h in FP64.  The
+// reflectors are those of the unblocked factorization up to rounding; each
+// half keeps its rows in shared memory where the whole panel would not fit,
+// and its columns see at most 127 trailing columns.  The Gram is built by
+// blocks: the leading block before the second half, then the blocks of the
+// second half's reflectors over rows h: (above them W~2 is zero), and only
+// the tiles on or below the diagonal of the symmetric blocks.
+int mixed_qr(MCtx& c, int64_t r, int64_t bi, double* P, int reserve) {
+  MixedWork& w = c.w;
+  constexpr int64_t h = 128;
+  if (bi <= h || r - h < bi - h) {
+    RUTV_TRY(launch_householder_qr(r, bi, P, r, w.W64, w.tau, w.qr, c.status + 2, c.status, c.st,
+                                   reserve));
+    RUTV_TRY(mixed_round_w(c, r, 0, bi));
+    return launch_dgemm(true, false, bi, bi, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, bi, w.dgemm,
+                        w.dgemm_bytes, c.st, true);
+  }
+  const int64_t h2 = bi - h;
+  RUTV_TRY(launch_householder_qr(r, h, P, r, w.W64, w.tau, w.qr, c.status + 2, c.status, c.st,
+                                 reserve));
+  RUTV_TRY(mixed_round_w(c, r, 0, h));
+  RUTV_TRY(launch_dgemm(true, false, h, h, r, 1.0, w.W64, r, w.W64, r, 0.0, w.Gram64, bi, w.dgemm,
+                        w.dgemm_bytes, c.st, true));
+  retau_kernel<<<1, 256, 0, c.st>>>((int)h, w.Gram64, bi, w.tau);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  RUTV_TRY(launch_wy_factor(h, w.Gram64, w.tau, w.S64, c.st, bi));
+  // P2 <- P2 - W~1 (S1^T (W~1^T P2)): the two long products on the tensor
+  // cores with the six-pair split (FP32-level, like every update of T), the
+  // h x h product by S1 in FP64
+  double* P2 = P + h * r;
+  RUTV_TRY(split_f64(P2, r, r, h2, 0, w.Pp, 0, 0, c.st));
+  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, h), opnd(w.Pp, 3, 0, 0, 0, r, h2), (int)h, (int)h2,
+                        (int)r, 3, out_f32(w.X, h), c.status, c.st, c.cap()));
+  RUTV_TRY(f32_to_f64(w.X, h, h, h2, w.qrX, h, c.st));
+  RUTV_TRY(launch_dgemm(true, false, h, h2, h, 1.0, w.S64, h, w.qrX, h, 0.0, w.qrY, h, w.dgemm,
+                        w.dgemm_bytes, c.st));
+  RUTV_TRY(split_f64(w.qrY, h, h, h2, 0, w.Sp, 0, 0, c.st));
+  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 1, r, h), opnd(w.Sp, 3, 0, 0, 0, h, h2), (int)r, (int)h2,
+                        (int)h, 3, out_f32(w.tmp, r), c.status, c.st, c.cap()));
+  {
+    ProfScope prof(K_CONVERT, 0.0, 20.0 * (double)r * h2, c.st);
+    const int64_t bx = (r + 255) / 256;
+    sub_f32_from_f64_kernel<<<dim3((unsigned)(bx < 64 ? bx : 64), (unsigned)h2), 256, 0, c.st>>>(
+        P2, r, w.tmp, r, r, h2);
+    note_launch();
+    RUTV_CK(cudaGetLastError());
+  }
+  RUTV_TRY(launch_householder_qr(r - h, h2, P2 + h, r, w.W2, w.tau + h, w.qr, c.status + 2,
+                                 c.status, c.st, reserve));
+  // W(:, h:) = [0; W2], rounded
+  double* Wr = w.W64 + h * r;
+  RUTV_CK(cudaMemset2DAsync(Wr, (size_t)r * 8, 0, (size_t)h * 8, (size_t)h2, c.st));
+  RUTV_CK(cudaMemcpy2DAsync(Wr + h, (size_t)r * 8, w.W2, (size_t)(r - h) * 8, (size_t)(r - h) * 8,
+                            (size_t)h2, cudaMemcpyDeviceToDevice, c.st));
+  RUTV_TRY(mixed_round_w(c, r, h, h2));
+  // Gram(h:, :h) = W~2^T W~1 and the lower part of Gram(h:, h:) = W~2^T W~2, rows h: only
+  RUTV_TRY(launch_dgemm(true, false, h2, h, r - h, 1.0, Wr + h, r, w.W64 + h, r, 0.0, w.Gram64 + h,
+                        bi, w.dgemm, w.dgemm_bytes, c.st));
+  return launch_dgemm(true, false, h2, h2, r - h, 1.0, Wr + h, r, Wr + h, r, 0.0,
+                      w.Gram64 + h + h * bi, bi, w.dgemm, w.dgemm_bytes, c.st, true);
 }
 
 // Joins the side stream and applies the pending row folds
@@ -386,7 +485,8 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
       RUTV_TRY(launch_bgemm(opnd(w.T, 1, k, k, 0), opnd_bf16(w.Yb, rm, bi, pad8(rm), 0), (int)rn,
                             (int)bi, (int)rm, 1, out_f32(w.Y, rn), c.status, c.st, c.cap()));
     }
-    RUTV_TRY(mixed_qr(c, rn, bi, w.Y, c.reserve()));
+    RUTV_TRY(f32_to_f64(w.Y, rn, rn, bi, w.Y64, rn, c.st));
+    RUTV_TRY(mixed_qr(c, rn, bi, w.Y64, c.reserve()));
     RUTV_TRY(mixed_wy(c, rn, bi));
     // X = T(:, k:) W (m x bi), then T(:, k:) -= X WS^T with X^T as planes
     RUTV_TRY(launch_bgemm(opnd(w.T, 3, 0, k, 1), opnd(w.W, 3, 0, 0, 0, rn, bi), (int)m, (int)bi, (int)rn, 3,
@@ -398,9 +498,9 @@ int mixed_step(MCtx& c, int step, int64_t k, int64_t bi) {
   }
   // ---------------- left transform
   if (rm > bi) {
-    RUTV_TRY(merge_f32(w.T, k, k, rm, bi, 0, w.Y, rm, c.st));
-    RUTV_TRY(mixed_qr(c, rm, bi, w.Y, c.reserve()));
-    RUTV_TRY(split_f32(w.Y, rm, rm, bi, 0, w.T, k, k, c.st));  // R and exact zeros
+    RUTV_TRY(merge_f64(w.T, k, k, rm, bi, 0, w.Y64, rm, c.st));
+    RUTV_TRY(mixed_qr(c, rm, bi, w.Y64, c.reserve()));
+    RUTV_TRY(split_f64(w.Y64, rm, rm, bi, 0, w.T, k, k, c.st));  // R and exact zeros
     RUTV_TRY(mixed_wy(c, rm, bi));
     if (rn > bi) {
       const int64_t nc = rn - bi;
