@@ -102,10 +102,11 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 struct BgemmParams {
   CUtensorMap ta[3];
   CUtensorMap tb[3];
-  CUtensorMap tc[3];   // mode 1: the output planes, box C_ROWS x BN, no swizzle (loads)
-  CUtensorMap tcs[3];  // mode 1: the same planes, box C_ROWS x EPI_COLS (stores)
+  CUtensorMap tcs[3];  // mode 1: the output planes, box C_ROWS x EPI_COLS, no swizzle
   int M, N, K;
   int tiles_n, ntiles, ksteps;
+  int ksplit, kchunk;      // split K: tile t = (output tile) * ksplit + chunk, kchunk K steps each
+  int64_t split_stride;    // elements between the partial products of two chunks (mode 0)
   int na, nb, npairs;   // planes of A and B, and pairs (the kernel's template argument)
   int a_mn;            // A MN-major
   int a_x0, a_y0;      // coordinate offsets of A's source (x = source row, y = source col)
@@ -131,11 +132,13 @@ struct BgemmParams {
 // out_upper, or no K step that can contribute).
 __device__ __forceinline__ bool tile_range(const BgemmParams& p, int tile, int& m0, int& n0,
                                            int& kb, int& ke) {
+  const int z = tile % p.ksplit;
+  tile /= p.ksplit;
   m0 = (tile / p.tiles_n) * BM;
   n0 = (tile % p.tiles_n) * BN;
   if (p.out_upper && m0 >= n0 + BN) return false;
-  kb = 0;
-  ke = p.ksteps;
+  kb = z * p.kchunk;
+  ke = min(p.ksteps, kb + p.kchunk);
   if (p.a_upper) kb = max(kb, m0 / BK);
   if (p.b_lower) kb = max(kb, n0 / BK);
   if (p.b_upper) ke = min(ke, (n0 + BN + BK - 1) / BK);
@@ -186,9 +189,8 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
   uint64_t* cor_full = acc_empty + 2;     // the chains of a segment (six pairs) or tile (one pair)
   uint64_t* cor_empty = cor_full + 1;
   uint64_t* mma_done = cor_empty + 1;
-  uint64_t* cfull = mma_done + 1;         // mode 1: output planes loaded
-  uint64_t* cfree = cfull + 1;            // mode 1: output planes stored (buffer free)
-  uint32_t* tmem_slot = (uint32_t*)(cfree + 1);
+  uint64_t* cw = mma_done + 1;            // [EPI_WARPS] mode 1: a warp's block of the planes loaded
+  uint32_t* tmem_slot = (uint32_t*)(cw + EPI_WARPS);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -204,8 +206,7 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     mbar_init(cor_full, 1);
     mbar_init(cor_empty, EPI_WARPS);
     mbar_init(mma_done, 1);
-    mbar_init(cfull, 1);
-    mbar_init(cfree, EPI_WARPS);
+    for (int e = 0; e < EPI_WARPS; ++e) mbar_init(&cw[e], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -223,8 +224,6 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     // ------------------------------------------------------------ producer
     if (lane == 0) {
       int g = 0;   // K steps issued over all tiles of this CTA
-      int tl = 0;  // tiles of this CTA
-      int cl = 0;  // output-plane loads issued
       bool run = true;
       for (int tile = blockIdx.x; run && tile < p.ntiles; tile += gridDim.x) {
         int m0, n0, kb, ke;
@@ -255,26 +254,11 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
             tma_load_2d(dst, &p.tb[j], &full[s], p.b_x0 + k0, p.b_y0 + n0);
           }
         }
-        if (run && p.mode == 1) {
-          // output planes of this tile, once the previous tile's have been stored
-          if (tl > 0 && !mbar_wait(cfree, (uint32_t)((tl - 1) & 1), p.err, 17)) {
-            run = false;
-          } else {
-            mbar_expect_tx(cfull, (uint32_t)(3 * C_TILE));
-            for (int i = 0; i < 3; ++i)
-              for (int sl = 0; sl < BM / C_ROWS; ++sl)
-                tma_load_2d(ctile + (size_t)i * C_ELEMS + (size_t)sl * C_SLICE, &p.tc[i], cfull,
-                            m0 + sl * C_ROWS, n0);
-            ++cl;
-          }
-        }
-        ++tl;
       }
       // let every copy issued land before the CTA can exit
       for (int k = (g > p.stages ? g - p.stages : 0); k < g; ++k) {
         mbar_wait(&full[k % p.stages], (uint32_t)((k / p.stages) & 1), p.err, 12);
       }
-      if (cl > 0) mbar_wait(cfull, (uint32_t)((cl - 1) & 1), p.err, 18);
     }
   } else if (warp == 1) {
     // ----------------------------------------------------------------- MMA
@@ -380,6 +364,7 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    const int ew = warp - 2;                          // epilogue warp index
     const int qd = warp & 3;                          // TMEM lane quadrant this warp may access
     const int c0 = ((warp - 2) >> 2) * EPI_COLS;      // its columns of the tile (warps 2..)
     const uint32_t lane_base = (uint32_t)(qd * 32) << 16;
@@ -389,6 +374,16 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     for (int tile = blockIdx.x; ok && tile < p.ntiles; tile += gridDim.x) {
       int m0, n0, kb, ke;
       if (!tile_range(p, tile, m0, n0, kb, ke)) continue;
+      // mode 1: this warp's block of the output planes (32 rows x EPI_COLS),
+      // loaded now so that the copy overlaps the drain; the previous tile's
+      // store has finished reading the buffer (bulk_wait_read below)
+      __nv_bfloat16* sl0 = ctile + (size_t)qd * C_SLICE + (size_t)c0 * C_ROWS;
+      if (p.mode == 1 && lane == 0) {
+        mbar_expect_tx(&cw[ew], (uint32_t)(3 * C_ROWS * EPI_COLS * 2));
+        for (int i = 0; i < 3; ++i)
+          tma_load_2d(sl0 + (size_t)i * C_ELEMS, &p.tcs[i], &cw[ew], m0 + qd * C_ROWS, n0 + c0);
+      }
+      const bool cpending = (p.mode == 1);
       float sum[EPI_COLS], cmp[EPI_COLS];
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) { sum[i] = 0.f; cmp[i] = 0.f; }
@@ -397,20 +392,21 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
         const int nch = min(kOneChains, (BK / 16) * (ke - kb));
         bool w = mbar_wait(cor_full, (uint32_t)(sg & 1), p.err, 14);
         ok = __all_sync(0xffffffffu, w) && ok;
-        if (!ok) break;
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        for (int ch = 0; ch < nch; ++ch) {
-          float v[EPI_COLS];
+        if (ok) {  // on failure fall through to the check below (copies in flight)
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          for (int ch = 0; ch < nch; ++ch) {
+            float v[EPI_COLS];
 #pragma unroll
-          for (int cc = 0; cc < EPI_COLS; cc += 32)
-            tmem_ld32(tmem + lane_base + (uint32_t)(ch * BN + c0 + cc), v + cc);
+            for (int cc = 0; cc < EPI_COLS; cc += 32)
+              tmem_ld32(tmem + lane_base + (uint32_t)(ch * BN + c0 + cc), v + cc);
 #pragma unroll
-          for (int i = 0; i < EPI_COLS; ++i) sum[i] += v[i];
+            for (int i = 0; i < EPI_COLS; ++i) sum[i] += v[i];
+          }
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(cor_empty);
+          ++sg;
         }
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(cor_empty);
-        ++sg;
       }
       for (int ks = kb; !kOnePair && ks < ke; ++ks, ++g) {
         const int buf = g & 1, use = g >> 1;
@@ -453,7 +449,11 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
         }
       }
       // warp-uniform: the lanes must not split before the next tcgen05.ld
-      if (__any_sync(0xffffffffu, !ok || *(volatile unsigned*)p.err != 0)) break;
+      if (__any_sync(0xffffffffu, !ok || *(volatile unsigned*)p.err != 0)) {
+        // let this warp's copy in flight land before the CTA can exit
+        if (cpending && lane == 0) mbar_wait(&cw[ew], (uint32_t)(tl & 1), p.err, 18);
+        break;
+      }
       // the tile's sum, rounded once to FP32
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) sum[i] += cmp[i];
@@ -462,7 +462,8 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
         if (p.mode == 0) {
           // read this row's C first: a store may alias the next column's
           // load, so interleaved they would wait one by one
-          float* crow = p.C + (int64_t)row + (int64_t)(n0 + c0) * p.ldc;
+          float* crow = p.C + (int64_t)(tile % p.ksplit) * p.split_stride + (int64_t)row +
+                        (int64_t)(n0 + c0) * p.ldc;
           const int ncol = min(EPI_COLS, p.N - (n0 + c0));
           if (p.beta != 0.f) {
             float cv[EPI_COLS];
@@ -483,9 +484,8 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
         // this warp's 32 rows x EPI_COLS columns of the tile's planes, in shared
         // memory (zero past the matrix edge); each warp stores its own block
         // back, so the epilogue warps never wait on one another
-        const bool w = mbar_wait(cfull, (uint32_t)(tl & 1), p.err, 19);
+        const bool w = mbar_wait(&cw[ew], (uint32_t)(tl & 1), p.err, 19);
         if (__any_sync(0xffffffffu, !w)) break;
-        __nv_bfloat16* sl0 = ctile + (size_t)qd * C_SLICE + (size_t)c0 * C_ROWS;
 #pragma unroll
         for (int i = 0; i < EPI_COLS; ++i) {
           const int o = i * C_ROWS + lane;
@@ -512,7 +512,6 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
             tma_store_2d(&p.tcs[i], sl0 + (size_t)i * C_ELEMS, m0 + qd * C_ROWS, n0 + c0);
           bulk_commit();
           bulk_wait_read();  // this block may be overwritten from here on
-          mbar_arrive(cfree);
         }
         __syncwarp();
       }
@@ -530,6 +529,20 @@ __global__ void __launch_bounds__(THREADS, 1) bgemm_kernel(const __grid_constant
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                  "r"(kTmemCols));
   }
+}
+
+// C = alpha sum_z P_z (the split-K partial products, M x N each, ld M), in
+// the order z = 0, 1, ...; columns by grid.y.
+__global__ void splitk_sum_kernel(int M, int N, int ks, const float* __restrict__ P, float alpha,
+                                  float* __restrict__ C, int64_t ldc) {
+  const int64_t MN = (int64_t)M * N;
+  for (int j = blockIdx.y; j < N; j += gridDim.y)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < M; i += gridDim.x * blockDim.x) {
+      const int64_t o = i + (int64_t)j * M;
+      float s = 0.f;
+      for (int z = 0; z < ks; ++z) s += P[z * MN + o];
+      C[i + (int64_t)j * ldc] = alpha * s;
+    }
 }
 
 // ---------------------------------------------------------------- host side
@@ -631,12 +644,9 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.stages = stages;
   p.mode = out.mode;
   if (out.mode == 1) {
-    for (int i = 0; i < 3; ++i) {
-      RUTV_TRY(make_tmap_box(&p.tc[i], out.planes[i], M, N, out.ldp, C_ROWS, BN,
-                             CU_TENSOR_MAP_SWIZZLE_NONE));
+    for (int i = 0; i < 3; ++i)
       RUTV_TRY(make_tmap_box(&p.tcs[i], out.planes[i], M, N, out.ldp, C_ROWS, EPI_COLS,
                              CU_TENSOR_MAP_SWIZZLE_NONE));
-    }
   }
   p.alpha = out.alpha;
   p.beta = out.beta;
@@ -651,6 +661,24 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.tiles_n = (N + BN - 1) / BN;
   p.ntiles = tiles_m * p.tiles_n;
   p.ksteps = (K + BK - 1) / BK;
+  p.ksplit = 1;
+  p.kchunk = p.ksteps;
+  p.split_stride = 0;
+  float* const c_final = out.C;
+  if (out.mode == 0 && out.beta == 0.f && out.ksplit > 1 && out.splitk_ws &&
+      !(tri.out_upper || tri.a_upper || tri.b_upper || tri.b_lower)) {
+    int64_t ks = std::min<int64_t>(out.ksplit, p.ksteps);
+    ks = std::min<int64_t>(ks, (int64_t)(out.splitk_floats / ((size_t)M * (size_t)N)));
+    if (ks > 1) {
+      p.kchunk = (int)((p.ksteps + ks - 1) / ks);
+      p.ksplit = (p.ksteps + p.kchunk - 1) / p.kchunk;  // every chunk non-empty
+      p.ntiles *= p.ksplit;
+      p.C = out.splitk_ws;  // partial products, M x N each (ld M), summed below
+      p.ldc = M;
+      p.alpha = 1.f;
+      p.split_stride = (int64_t)M * N;
+    }
+  }
   p.out_upper = tri.out_upper;
   p.a_upper = tri.a_upper;
   p.b_upper = tri.b_upper;
@@ -672,7 +700,10 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
       mma_flops += 2.0 * rows * cols * kk * p.npairs;
     }
   }
-  const size_t smem = 1024 + (size_t)stages * per_stage + ctile_bytes + (2 * stages + 11) * 8 + 16;
+  // barriers: full and empty per stage, two lead, the chains' pair, mma_done,
+  // one per epilogue warp; then the TMEM address
+  const size_t smem =
+      1024 + (size_t)stages * per_stage + ctile_bytes + (2 * stages + 7 + EPI_WARPS) * 8 + 16;
   const void* fn = (p.npairs == 6) ? (const void*)bgemm_kernel<6> : (const void*)bgemm_kernel<1>;
   RUTV_TRY(ensure_smem(fn, smem));
   // persistent: at most one CTA per SM (the shared memory allows no more)
@@ -687,6 +718,13 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   else bgemm_kernel<1><<<grid, THREADS, smem, st>>>(p);
   note_launch();
   RUTV_CK(cudaGetLastError());
+  if (p.ksplit > 1) {
+    const int64_t bx = std::min<int64_t>((M + 255) / 256, 64);
+    splitk_sum_kernel<<<dim3((unsigned)bx, (unsigned)std::min(N, 65535)), 256, 0, st>>>(
+        M, N, p.ksplit, out.splitk_ws, out.alpha, c_final, out.ldc);
+    note_launch();
+    RUTV_CK(cudaGetLastError());
+  }
   return 0;
 }
 

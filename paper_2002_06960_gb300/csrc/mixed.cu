@@ -356,8 +356,15 @@ int mixed_qr(MCtx& c, int64_t r, int64_t bi, double* P, int reserve) {
   // h x h product by S1 in FP64
   double* P2 = P + h * r;
   RUTV_TRY(split_f64(P2, r, r, h2, 0, w.Pp, 0, 0, c.st));
-  RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, h), opnd(w.Pp, 3, 0, 0, 0, r, h2), (int)h, (int)h2,
-                        (int)r, 3, out_f32(w.X, h), c.status, c.st, c.cap()));
+  {
+    // a 128 x 128 output over K = r: split K across the SMs (partials in Z)
+    BgemmOut ox = out_f32(w.X, h);
+    ox.ksplit = (c.cap() > 0 ? c.cap() : dev_info().sms) / 2;
+    ox.splitk_ws = w.Z;
+    ox.splitk_floats = (size_t)(c.m > c.n ? c.m : c.n) * (size_t)c.b;  // Z: max(m, n) x b
+    RUTV_TRY(launch_bgemm(opnd(w.W, 3, 0, 0, 0, r, h), opnd(w.Pp, 3, 0, 0, 0, r, h2), (int)h,
+                          (int)h2, (int)r, 3, ox, c.status, c.st, c.cap()));
+  }
   RUTV_TRY(f32_to_f64(w.X, h, h, h2, w.qrX, h, c.st));
   RUTV_TRY(launch_dgemm(true, false, h, h2, h, 1.0, w.S64, h, w.qrX, h, 0.0, w.qrY, h, w.dgemm,
                         w.dgemm_bytes, c.st));

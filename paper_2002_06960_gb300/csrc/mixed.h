@@ -41,6 +41,12 @@ struct BgemmOut {
   int64_t ldc = 0;
   __nv_bfloat16* planes[3] = {nullptr, nullptr, nullptr};
   int64_t ldp = 0;
+  // mode 0 with beta = 0: split K over up to `ksplit` partial products held
+  // in `splitk_ws` (ksplit M x N floats), then summed in a fixed order, for
+  // outputs with too few tiles to occupy the SMs; capped by splitk_floats.
+  int ksplit = 1;
+  float* splitk_ws = nullptr;
+  size_t splitk_floats = 0;
 };
 
 // Structure of the operands that lets tiles or K steps be skipped:
