@@ -208,6 +208,14 @@ __global__ void axpy_kernel(int64_t n, double a, const double* x, double* y) {
     y[e] = fma(a, x[e], y[e]);
 }
 
+// B = A^T (n x n, ld n)
+__global__ void transpose_kernel(int n, const double* __restrict__ A, double* __restrict__ B) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < n * n; e += gridDim.x * blockDim.x) {
+    const int i = e % n, j = e / n;
+    B[j + (int64_t)i * n] = A[e];
+  }
+}
+
 __global__ void eye_kernel(int64_t rows, int64_t cols, double* X, int64_t ld) {
   const int64_t total = rows * cols;
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
@@ -355,7 +363,8 @@ int larft_reverse(LCtx& c, int64_t r, int64_t b, const double* W, const double* 
 struct StepState {
   int64_t k, rm, rn;
   bool right, left;
-  double *M, *N, *Upre;          // input of the step, after the right transform, U(:, k:) before
+  double *M, *N;                 // input of the step, and after the right transform
+  double* Xin;                   // U_k chain: the block U(k:m, k:kk) before Q_U of this step
   double *Ych, *Zch;             // power chain: Y_0..Y_q (rn x b each), Z_0..Z_{q-1}
   double *PV, *WV, *tauV, *SV, *GV;  // sketch QR: final panel, reflectors, WY factor, Gram
   double *PU, *WU, *tauU, *SU, *GU;  // panel QR of the new block column
@@ -405,8 +414,6 @@ int lowrank_forward(LCtx& c, Pool& pool, int64_t m, int64_t n, const double* A, 
   double* Min = pool.get((size_t)m * n);
   if (!Min) return RANDUTV_ENOMEM;
   RUTV_TRY(copy(c, Min, m, A, lda, m, n));
-  eye_kernel<<<grid_of(m * m), 256, 0, c.st>>>(m, m, U, m);
-  note_launch();
   double* t = pool.get((size_t)(m > n ? m : n) * b);
   if (!t) return RANDUTV_ENOMEM;
   (void)ap;
@@ -420,9 +427,7 @@ int lowrank_forward(LCtx& c, Pool& pool, int64_t m, int64_t n, const double* A, 
     S.M = Min;
     const int64_t rm = S.rm, rn = S.rn;
     S.N = pool.get((size_t)rm * rn);
-    S.Upre = pool.get((size_t)m * rm);
-    if (!S.N || !S.Upre) return RANDUTV_ENOMEM;
-    RUTV_TRY(copy(c, S.Upre, m, U + S.k * m, m, m, rm));
+    if (!S.N) return RANDUTV_ENOMEM;
     if (S.right) {
       S.Ych = pool.get((size_t)(q + 1) * rn * b);
       S.Zch = pool.get((size_t)(q > 0 ? q : 1) * rm * b);
@@ -474,13 +479,27 @@ int lowrank_forward(LCtx& c, Pool& pool, int64_t m, int64_t n, const double* A, 
     double* Mnext = pool.get((size_t)(rm - b) * nc);
     if (!Mnext) return RANDUTV_ENOMEM;
     RUTV_TRY(copy(c, Mnext, rm - b, Nr + b, rm, rm - b, nc));
-    // U(:, k:) <- U(:, k:) Q_U
-    RUTV_TRY(G(c, false, false, m, b, rm, 1.0, U + S.k * m, m, S.WU, rm, 0.0, t, m));
-    double* t3 = pool.get((size_t)m * b);
-    if (!t3) return RANDUTV_ENOMEM;
-    RUTV_TRY(G(c, false, false, m, b, b, 1.0, t, m, S.SU, b, 0.0, t3, m));
-    RUTV_TRY(G(c, false, true, m, rm, b, -1.0, t3, m, S.WU, rm, 1.0, U + S.k * m, m));
     Min = Mnext;
+  }
+  // U_k = Qt_0 (Qt_1 (... (Qt_{s-1} E_k))), Qt_i = diag(I_{k_i}, Q_U of step i), the first
+  // k columns of the product the blocked loop accumulates into U.  Step i changes only the
+  // block U(k_i:m, k_i:k), so the chain costs O(m k b) per step instead of O(m^2 b); the
+  // block's input is kept for the reverse.
+  eye_kernel<<<grid_of(m * (int64_t)k), 256, 0, c.st>>>(m, k, U, m);
+  note_launch();
+  double* wk = pool.get((size_t)b * k);
+  double* wk2 = pool.get((size_t)b * k);
+  if (!wk || !wk2) return RANDUTV_ENOMEM;
+  for (int i = s - 1; i >= 0; --i) {
+    StepState& S = st[i];
+    const int64_t r = S.rm, cc = k - S.k;
+    double* X = U + S.k + S.k * m;
+    S.Xin = pool.get((size_t)r * cc);
+    if (!S.Xin) return RANDUTV_ENOMEM;
+    RUTV_TRY(copy(c, S.Xin, r, X, m, r, cc));
+    RUTV_TRY(G(c, true, false, b, cc, r, 1.0, S.WU, r, X, m, 0.0, wk, b));      // W^T X
+    RUTV_TRY(G(c, false, false, b, cc, b, 1.0, S.SU, b, wk, b, 0.0, wk2, b));   // S W^T X
+    RUTV_TRY(G(c, false, false, r, cc, b, -1.0, S.WU, r, wk2, b, 1.0, X, m));   // Q_U X
   }
   return 0;
 }
@@ -564,18 +583,42 @@ int randutv_lowrank_backward(int64_t m, int64_t n, const double* A, int64_t lda,
   RUTV_TRY(G(c, false, false, m, k, n, 1.0, A, lda, AkU, n, 1.0, Ub, m));
   RUTV_TRY(G(c, true, false, k, n, m, 1.0, U, m, dAk, m, 0.0, UtA, k));
   RUTV_TRY(G(c, false, false, m, n, k, 1.0, U, m, UtA, k, 0.0, dA, m));
+  // The U_k chain backwards (its forward ran from the last step to the first, so its reverse
+  // runs from the first): the block X_i = Q_U X_{i+1} with Q_U = I - W S W^T is the left
+  // application X -> Q'^T X with Q' = I - W S^T W^T, whose adjoint left_apply_rev gives
+  // (with S^T in place of S, and the S adjoint transposed back).  The W and S adjoints of each
+  // step are kept for the step's panel-QR reverse below.
+  const int ns = (int)st.size();
+  std::vector<double*> WbU(ns), SbU(ns);
+  double* SUt = pool.get((size_t)b * b);
+  double* SbUt = pool.get((size_t)b * b);
+  if (!SUt || !SbUt) return RANDUTV_ENOMEM;
+  for (int i = 0; i < ns; ++i) {
+    StepState& S = st[i];
+    const int64_t r = S.rm, cc = k - S.k;
+    WbU[i] = pool.get((size_t)r * b);
+    SbU[i] = pool.get((size_t)b * b);
+    if (!WbU[i] || !SbU[i]) return RANDUTV_ENOMEM;
+    RUTV_TRY(zero(c, WbU[i], (size_t)r * b));
+    RUTV_TRY(zero(c, SbUt, (size_t)b * b));
+    transpose_kernel<<<grid_of((int64_t)b * b), 256, 0, c.st>>>(b, S.SU, SUt);
+    note_launch();
+    double* Xb = Ub + S.k + S.k * m;  // adjoint of the block, updated in place
+    RUTV_TRY(left_apply_rev(c, r, cc, b, S.Xin, r, Xb, m, S.WU, SUt, Xb, m, WbU[i], SbUt, t1, t2,
+                            t3));
+    transpose_kernel<<<grid_of((int64_t)b * b), 256, 0, c.st>>>(b, SbUt, SbU[i]);
+    note_launch();
+  }
+  RUTV_CK(cudaGetLastError());
   // adjoint of the input of the step after the last one: zero
   double* Mb_next = nullptr;
-  for (int i = (int)st.size() - 1; i >= 0; --i) {
+  for (int i = ns - 1; i >= 0; --i) {
     StepState& S = st[i];
     const int64_t rm = S.rm, rn = S.rn, nc = rn - b;
-    // ---- U(:, k:) <- U(:, k:) Q_U  (right application on U_pre)
-    RUTV_TRY(zero(c, Wb, (size_t)rm * b));
-    RUTV_TRY(zero(c, Sb, (size_t)b * b));
+    // ---- the step's W_U and S_U adjoints start from the U_k chain's
+    RUTV_TRY(copy(c, Wb, rm, WbU[i], rm, rm, b));
+    RUTV_TRY(copy(c, Sb, b, SbU[i], b, b, b));
     RUTV_TRY(zero(c, taub, b));
-    RUTV_TRY(copy(c, Ob, m, Ub + S.k * m, m, m, rm));
-    RUTV_TRY(right_apply_rev(c, m, rm, b, S.Upre, m, Ob, m, S.WU, S.SU, Ub + S.k * m, m, Wb, Sb,
-                             t1, t2, t3));
     // ---- M_{i+1} = (Q_U^T N(:, b:))(b:, b:)
     RUTV_TRY(zero(c, Ob, (size_t)rm * nc));
     if (Mb_next) RUTV_TRY(copy(c, Ob + b, rm, Mb_next, rm - b, rm - b, nc));
