@@ -310,10 +310,13 @@ int hqr_reverse(LCtx& c, int64_t r, int64_t b, double* X, const double* W, const
 
 // Adjoints of X -> X Q (right) for Q = I - W S W^T (X rows x cols, W cols x b):
 // Xb = Ob Q^T (written into Xb), Sb += -(XW)^T (ObW), Wb += -X^T ObW S^T - Ob^T XW S.
+// XW: X W kept from the forward (rows x b, ld rows), or null to recompute it into t1.
 int right_apply_rev(LCtx& c, int64_t rows, int64_t cols, int64_t b, const double* X, int64_t ldx,
                     const double* Ob, int64_t ldo, const double* W, const double* S, double* Xb,
-                    int64_t ldxb, double* Wb, double* Sb, double* t1, double* t2, double* t3) {
-  RUTV_TRY(G(c, false, false, rows, b, cols, 1.0, X, ldx, W, cols, 0.0, t1, rows));    // XW
+                    int64_t ldxb, double* Wb, double* Sb, double* t1, double* t2, double* t3,
+                    const double* XW = nullptr) {
+  if (XW) t1 = const_cast<double*>(XW);  // read only below
+  else RUTV_TRY(G(c, false, false, rows, b, cols, 1.0, X, ldx, W, cols, 0.0, t1, rows));  // XW
   RUTV_TRY(G(c, false, false, rows, b, cols, 1.0, Ob, ldo, W, cols, 0.0, t2, rows));   // ObW
   RUTV_TRY(G(c, true, false, b, b, rows, -1.0, t1, rows, t2, rows, 1.0, Sb, b));       // Sb
   RUTV_TRY(G(c, false, true, rows, b, b, 1.0, t2, rows, S, b, 0.0, t3, rows));         // ObW S^T
@@ -328,20 +331,23 @@ int right_apply_rev(LCtx& c, int64_t rows, int64_t cols, int64_t b, const double
 
 // Adjoints of X -> Q^T X (left) for Q = I - W S W^T (X rows x cols, W rows x b):
 // Xb = Q Ob, Sb += -(W^T X)(W^T Ob)^T, Wb += -Ob (W^T X)^T S - X (W^T Ob)^T S^T.
+// WX: W^T X kept from the forward (b x cols, ld b), or null to recompute it into t1.
 int left_apply_rev(LCtx& c, int64_t rows, int64_t cols, int64_t b, const double* X, int64_t ldx,
                    const double* Ob, int64_t ldo, const double* W, const double* S, double* Xb,
-                   int64_t ldxb, double* Wb, double* Sb, double* t1, double* t2, double* t3) {
-  RUTV_TRY(G(c, true, false, b, cols, rows, 1.0, W, rows, X, ldx, 0.0, t1, b));     // WX
+                   int64_t ldxb, double* Wb, double* Sb, double* t1, double* t2, double* t3,
+                   const double* WX = nullptr) {
+  if (WX) t1 = const_cast<double*>(WX);  // read only below
+  else RUTV_TRY(G(c, true, false, b, cols, rows, 1.0, W, rows, X, ldx, 0.0, t1, b));  // WX
   RUTV_TRY(G(c, true, false, b, cols, rows, 1.0, W, rows, Ob, ldo, 0.0, t2, b));    // WOb
   RUTV_TRY(G(c, false, true, b, b, cols, -1.0, t1, b, t2, b, 1.0, Sb, b));          // Sb
   RUTV_TRY(G(c, true, false, cols, b, b, 1.0, t1, b, S, b, 0.0, t3, cols));         // WX^T S (cols x b)
   RUTV_TRY(G(c, false, false, rows, b, cols, -1.0, Ob, ldo, t3, cols, 1.0, Wb, rows));
   RUTV_TRY(G(c, true, true, cols, b, b, 1.0, t2, b, S, b, 0.0, t3, cols));          // WOb^T S^T
   RUTV_TRY(G(c, false, false, rows, b, cols, -1.0, X, ldx, t3, cols, 1.0, Wb, rows));
-  // Xb = Ob - W S (W^T Ob)
-  RUTV_TRY(G(c, false, false, b, cols, b, 1.0, S, b, t2, b, 0.0, t1, b));           // S WOb
+  // Xb = Ob - W S (W^T Ob)   (S WOb into t3, free again; t1 may be the forward's W^T X)
+  RUTV_TRY(G(c, false, false, b, cols, b, 1.0, S, b, t2, b, 0.0, t3, b));           // S WOb
   if (Xb != Ob) RUTV_TRY(copy(c, Xb, ldxb, Ob, ldo, rows, cols));
-  RUTV_TRY(G(c, false, false, rows, cols, b, -1.0, W, rows, t1, b, 1.0, Xb, ldxb));
+  RUTV_TRY(G(c, false, false, rows, cols, b, -1.0, W, rows, t3, b, 1.0, Xb, ldxb));
   return 0;
 }
 
@@ -365,6 +371,7 @@ struct StepState {
   bool right, left;
   double *M, *N;                 // input of the step, and after the right transform
   double* Xin;                   // U_k chain: the block U(k:m, k:kk) before Q_U of this step
+  double *MW, *WN;               // forward products kept for the reverse: M W_V, W_U^T N(:, b:)
   double *Ych, *Zch;             // power chain: Y_0..Y_q (rn x b each), Z_0..Z_{q-1}
   double *PV, *WV, *tauV, *SV, *GV;  // sketch QR: final panel, reflectors, WY factor, Gram
   double *PU, *WU, *tauU, *SU, *GU;  // panel QR of the new block column
@@ -414,8 +421,6 @@ int lowrank_forward(LCtx& c, Pool& pool, int64_t m, int64_t n, const double* A, 
   double* Min = pool.get((size_t)m * n);
   if (!Min) return RANDUTV_ENOMEM;
   RUTV_TRY(copy(c, Min, m, A, lda, m, n));
-  double* t = pool.get((size_t)(m > n ? m : n) * b);
-  if (!t) return RANDUTV_ENOMEM;
   (void)ap;
   for (int i = 0; i < s; ++i) {
     StepState& S = st[i];
@@ -451,10 +456,11 @@ int lowrank_forward(LCtx& c, Pool& pool, int64_t m, int64_t n, const double* A, 
       RUTV_TRY(hqr_wy(c, rn, b, S.PV, S.WV, S.tauV, S.GV, S.SV));
       // N = M Q_V
       RUTV_TRY(copy(c, S.N, rm, S.M, rm, rm, rn));
-      RUTV_TRY(G(c, false, false, rm, b, rn, 1.0, S.M, rm, S.WV, rn, 0.0, t, rm));
+      S.MW = pool.get((size_t)rm * b);
       double* t2 = pool.get((size_t)rm * b);
-      if (!t2) return RANDUTV_ENOMEM;
-      RUTV_TRY(G(c, false, false, rm, b, b, 1.0, t, rm, S.SV, b, 0.0, t2, rm));
+      if (!S.MW || !t2) return RANDUTV_ENOMEM;
+      RUTV_TRY(G(c, false, false, rm, b, rn, 1.0, S.M, rm, S.WV, rn, 0.0, S.MW, rm));
+      RUTV_TRY(G(c, false, false, rm, b, b, 1.0, S.MW, rm, S.SV, b, 0.0, t2, rm));
       RUTV_TRY(G(c, false, true, rm, rn, b, -1.0, t2, rm, S.WV, rn, 1.0, S.N, rm));
     } else {
       RUTV_TRY(copy(c, S.N, rm, S.M, rm, rm, rn));
@@ -474,6 +480,7 @@ int lowrank_forward(LCtx& c, Pool& pool, int64_t m, int64_t n, const double* A, 
     const int64_t nc = rn - b;
     RUTV_TRY(copy(c, Nr, rm, S.N + b * rm, rm, rm, nc));
     RUTV_TRY(G(c, true, false, b, nc, rm, 1.0, S.WU, rm, Nr, rm, 0.0, wx, b));        // W^T X
+    S.WN = wx;  // kept for the reverse
     RUTV_TRY(G(c, true, false, b, nc, b, 1.0, S.SU, b, wx, b, 0.0, wx2, b));           // S^T W^T X
     RUTV_TRY(G(c, false, false, rm, nc, b, -1.0, S.WU, rm, wx2, b, 1.0, Nr, rm));      // Q^T X
     double* Mnext = pool.get((size_t)(rm - b) * nc);
@@ -624,7 +631,7 @@ int randutv_lowrank_backward(int64_t m, int64_t n, const double* A, int64_t lda,
     if (Mb_next) RUTV_TRY(copy(c, Ob + b, rm, Mb_next, rm - b, rm - b, nc));
     RUTV_TRY(zero(c, Nb, (size_t)rm * rn));
     RUTV_TRY(left_apply_rev(c, rm, nc, b, S.N + b * rm, rm, Ob, rm, S.WU, S.SU, Nb + b * rm, rm,
-                            Wb, Sb, t1, t2, t3));
+                            Wb, Sb, t1, t2, t3, S.WN));
     // ---- panel QR of N(:, 0:b)
     RUTV_TRY(larft_reverse(c, rm, b, S.WU, S.tauU, S.SU, S.GU, Sb, Wb, taub, Gb));
     keep_strict_lower<<<grid_of(rm * b), 256, 0, c.st>>>(rm, b, Wb);
@@ -637,7 +644,7 @@ int randutv_lowrank_backward(int64_t m, int64_t n, const double* A, int64_t lda,
       RUTV_TRY(zero(c, Sb, (size_t)b * b));
       RUTV_TRY(zero(c, taub, b));
       RUTV_TRY(right_apply_rev(c, rm, rn, b, S.M, rm, Nb, rm, S.WV, S.SV, Mb, rm, Wb, Sb, t1, t2,
-                               t3));
+                               t3, S.MW));
       RUTV_TRY(larft_reverse(c, rn, b, S.WV, S.tauV, S.SV, S.GV, Sb, Wb, taub, Gb));
       keep_strict_lower<<<grid_of(rn * b), 256, 0, c.st>>>(rn, b, Wb);
       note_launch();
