@@ -18,6 +18,8 @@
 #include <utility>
 #include <vector>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.h"
 #include "mixed.h"
@@ -627,8 +629,20 @@ int randutv_gemm_bf16(char transa, int64_t M, int64_t N, int64_t K, float alpha,
   if (M > (1 << 30) || N > (1 << 30) || K > (1 << 30)) return RANDUTV_EUNSUPPORTED;
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t ar_rows = ta ? K : M, ar_cols = ta ? M : K;
+  // beta = 0 and an output of few 128 x 64 tiles over a long K: split K across the SMs
+  // (partial products in the scratch, at most 64 MB of them, summed in a fixed order)
+  const int64_t tiles = ((M + 127) / 128) * ((N + 63) / 64);
+  const int sms = dev_info().sms;
+  int64_t ks = 1;
+  size_t ws_floats = 0;
+  if (beta == 0.f && 2 * tiles <= sms && K >= 1024) {
+    ks = std::min<int64_t>(sms / tiles, (K + 63) / 64);
+    ks = std::min<int64_t>(ks, (int64_t)(((size_t)16 << 20) / ((size_t)M * (size_t)N)));
+    if (ks > 1) ws_floats = (size_t)ks * (size_t)M * (size_t)N;
+  }
   Arena ar;
-  RUTV_TRY(scratch_reserve(planes_bytes(ar_rows, ar_cols) + planes_bytes(K, N) + 4096, &ar));
+  RUTV_TRY(scratch_reserve(planes_bytes(ar_rows, ar_cols) + planes_bytes(K, N) + ws_floats * 4 +
+                               4096, &ar));
   unsigned* status = nullptr;
   RUTV_TRY(status_words(&status));
   RUTV_CK(cudaMemsetAsync(status, 0, 64 * sizeof(unsigned), st));
@@ -636,8 +650,14 @@ int randutv_gemm_bf16(char transa, int64_t M, int64_t N, int64_t K, float alpha,
   Planes Pb = carve_planes(ar, K, N);
   RUTV_TRY(split_f32(A, lda, ar_rows, ar_cols, 0, Pa, 0, 0, st));
   RUTV_TRY(split_f32(B, ldb, K, N, 0, Pb, 0, 0, st));
+  BgemmOut out = out_f32(C, ldc, alpha, beta);
+  if (ws_floats > 0) {
+    out.ksplit = (int)ks;
+    out.splitk_ws = (float*)ar.take(ws_floats * 4);
+    out.splitk_floats = ws_floats;
+  }
   return launch_bgemm(opnd(Pa, planes, 0, 0, ta ? 0 : 1), opnd(Pb, planes, 0, 0, 0), (int)M,
-                      (int)N, (int)K, planes, out_f32(C, ldc, alpha, beta), status, st);
+                      (int)N, (int)K, planes, out, status, st);
 }
 
 }  // extern "C"

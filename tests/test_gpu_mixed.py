@@ -71,6 +71,31 @@ def test_bgemm_one_plane_is_the_bf16_product(pkg, transa, M, N, K):
     assert err <= 1e-5 * (K ** 0.5) * 4, err
 
 
+@pytest.mark.parametrize("planes", [3, 1])
+@pytest.mark.parametrize("transa,M,N,K", [("T", 128, 128, 16384), ("N", 200, 96, 5000),
+                                          ("T", 64, 40, 1030)])
+def test_bgemm_split_k(pkg, planes, transa, M, N, K):
+    """beta = 0 with few output tiles over a long K takes the split-K path (partial
+    products summed in a fixed order): the same accuracy bounds as the plain path."""
+    g = torch.Generator().manual_seed(M + N + K + planes)
+    A = torch.randn((K, M) if transa == "T" else (M, K), generator=g, dtype=f64).to(f32)
+    B = torch.randn(K, N, generator=g, dtype=f64).to(f32)
+    Cd = colmajor(pkg, torch.full((M, N), float("nan")))  # beta = 0: C is not read
+    pkg.randutv_gemm_bf16(transa, 0.5, colmajor(pkg, A), colmajor(pkg, B), 0.0, Cd, planes=planes)
+    torch.cuda.synchronize()
+    got = Cd.cpu().double()
+    if planes == 3:
+        ref = 0.5 * ((A.double().T if transa == "T" else A.double()) @ B.double())
+        ref32 = 0.5 * ((A.T if transa == "T" else A) @ B)
+        err32 = (ref32.double() - ref).abs().max().item()
+        bound = 2.0 * K * 2.0 ** -24 * (A.double().abs().max() * B.double().abs().max()).item()
+        assert (got - ref).abs().max().item() <= max(4.0 * err32, 1e-7) + 0.25 * bound
+    else:
+        Ab, Bb = A.to(torch.bfloat16).double(), B.to(torch.bfloat16).double()
+        ref = 0.5 * ((Ab.T if transa == "T" else Ab) @ Bb)
+        assert (got - ref).abs().max().item() <= 1e-5 * (K ** 0.5) * 4
+
+
 def _mixed(pkg, A, b, q, seed):
     U, T, V = pkg.randutv_factor_mixed(colmajor(pkg, A), b, q, seed)
     assert pkg.randutv_stream_status() == 0
