@@ -865,9 +865,9 @@ def oracle_sample(n, b, q, seed, steps, A=None):
                       f"factorization with U and V ({flops:.3e} algorithmic flops, {dt:.1f} s)"}
 
 
-def cpu_sweep(args, sizes=(512, 1024, 2048), b=128, q=1):
+def cpu_sweep(args, sizes=(512, 1024, 2048, 4096), b=128, q=1):
     """The CPU oracle on whole factorizations (U, T, V), i.i.d. N(0,1), median
-    of 3 (1 at 2048); larger n extrapolated by t / n^3 and labelled so."""
+    of 3 (1 from 2048 on); larger n extrapolated by t / n^3 and labelled so."""
     import oracle
     rows = []
     for n in sizes:
@@ -883,7 +883,7 @@ def cpu_sweep(args, sizes=(512, 1024, 2048), b=128, q=1):
         rows.append({"n": n, "seconds": round(t, 3), "tflops": round(fl / t / 1e12, 4),
                      "t_over_n3_e10": round(t / n ** 3 * 1e10, 4), "measured": True})
     c = rows[-1]["t_over_n3_e10"]
-    for n in (4096, 8192, 16384):
+    for n in (8192, 16384):
         t = c * n ** 3 / 1e10
         rows.append({"n": n, "seconds": round(t, 1),
                      "tflops": round(inputs.algorithmic_flops(n, n, b, q) / t / 1e12, 4),
