@@ -19,9 +19,13 @@
 // A_0 B_0 (one per K step, alternating) and six chains for the correction
 // products of the split (one segment of K steps at a time); a one-pair
 // product spreads each tile over all eight, so that every FP32 accumulation
-// in TMEM stays short.  Warp 0 issues TMA loads (and owns the TMEM allocation), warp 1 issues the
-// MMAs, and warps 2-9 drain the accumulators, two warps per 32-lane quadrant,
-// each on half the columns.
+// in TMEM stays short.  Warp 0 issues TMA loads (and owns the TMEM
+// allocation), warp 1 issues the MMAs, and warps 2-9 drain the accumulators,
+// two warps per 32-lane quadrant, each on half the columns; in plane updates
+// each of them also loads and stores its own 32 x 32 block of the output
+// planes by TMA.  An FP32 output with few tiles can split K into chunks run
+// as extra tiles, whose partial products a second kernel sums in a fixed
+// order.
 // Every mbarrier wait is bounded; on timeout the kernel records
 // RANDUTV_ETIMEOUT, lets its copies in flight land, frees TMEM and returns.
 #include <algorithm>
@@ -120,16 +124,13 @@ struct BgemmParams {
   float alpha, beta;
   float* C;            // mode 0
   int64_t ldc;
-  __nv_bfloat16* P0;   // mode 1 planes, same ld
-  __nv_bfloat16* P1;
-  __nv_bfloat16* P2;
-  int64_t ldp;
   unsigned* err;
 };
 
-// Output tile `tile` of the persistent order: its corner and its K steps
-// [kb, ke); false when the tile is skipped (wholly below the diagonal with
-// out_upper, or no K step that can contribute).
+// Output tile `tile` of the persistent order (with split K: output tile
+// tile / ksplit, K chunk tile % ksplit): its corner and its K steps [kb, ke);
+// false when the tile is skipped (wholly below the diagonal with out_upper, or
+// no K step that can contribute).
 __device__ __forceinline__ bool tile_range(const BgemmParams& p, int tile, int& m0, int& n0,
                                            int& kb, int& ke) {
   const int z = tile % p.ksplit;
@@ -652,10 +653,6 @@ int launch_bgemm(const BgemmOperand& A, const BgemmOperand& B, int M, int N, int
   p.beta = out.beta;
   p.C = out.C;
   p.ldc = out.ldc;
-  p.P0 = out.planes[0];
-  p.P1 = out.planes[1];
-  p.P2 = out.planes[2];
-  p.ldp = out.ldp;
   p.err = err;
   const int tiles_m = (M + BM - 1) / BM;
   p.tiles_n = (N + BN - 1) / BN;
