@@ -334,6 +334,9 @@ int qr_launch(QrArgsT<Real>& a, int nb, cudaStream_t st) {
 constexpr int WY_WARPS = 1;   // one column per CTA: the FP64 work spreads over the SMs
 constexpr int WY_MAXC = 256;
 
+// kInverse: M = (I + D_tau striu(Gm))^-1 instead, M(i, k) = delta_ik - tau_i sum_l Gm(i, l)
+// M(l, k) (S = M D_tau; M is needed apart from S where some tau is zero).
+template <bool kInverse>
 __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const double* __restrict__ Gm,
                                                                    int64_t ldg,
                                                                    const double* __restrict__ tau,
@@ -371,7 +374,10 @@ __global__ void __launch_bounds__(WY_WARPS * 32) wy_factor_kernel(int c, const d
       }
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) sk[i] = tcur * (((i == k) ? 1.0 : 0.0) - acc);
+    if (lane == 0) {
+      if (kInverse) sk[i] = ((i == k) ? 1.0 : 0.0) - tcur * acc;
+      else sk[i] = tcur * (((i == k) ? 1.0 : 0.0) - acc);
+    }
     __syncwarp();
 #pragma unroll
     for (int t = 0; t < NL; ++t) gcur[t] = gnext[t];
@@ -407,8 +413,19 @@ int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, 
   if (ldg == 0) ldg = c;
   if (ldg < c) return RANDUTV_EUNSUPPORTED;
   ProfScope prof(K_WY, (double)c * c * c / 3.0, 16.0 * (double)c * c, st);
-  wy_factor_kernel<<<(unsigned)((c + WY_WARPS - 1) / WY_WARPS), WY_WARPS * 32, 0, st>>>((int)c, Gm,
-                                                                                        ldg, tau, S);
+  wy_factor_kernel<false><<<(unsigned)((c + WY_WARPS - 1) / WY_WARPS), WY_WARPS * 32, 0, st>>>(
+      (int)c, Gm, ldg, tau, S);
+  note_launch();
+  RUTV_CK(cudaGetLastError());
+  return 0;
+}
+
+int launch_wy_inverse(int64_t c, const double* Gm, const double* tau, double* M, cudaStream_t st) {
+  if (c <= 0) return 0;
+  if (c > WY_MAXC) return RANDUTV_EUNSUPPORTED;
+  ProfScope prof(K_ADJOINT, (double)c * c * c / 3.0, 16.0 * (double)c * c, st);
+  wy_factor_kernel<true><<<(unsigned)((c + WY_WARPS - 1) / WY_WARPS), WY_WARPS * 32, 0, st>>>(
+      (int)c, Gm, c, tau, M);
   note_launch();
   RUTV_CK(cudaGetLastError());
   return 0;

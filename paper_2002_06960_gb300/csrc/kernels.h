@@ -35,6 +35,8 @@ int launch_householder_qr(int64_t r, int64_t c, double* A, int64_t lda, double* 
 // strictly lower part are read, leading dimension ldg; 0 means c) and tau.
 int launch_wy_factor(int64_t c, const double* Gm, const double* tau, double* S, cudaStream_t st,
                      int64_t ldg = 0);
+// M = (I + D_tau striu(Gm))^-1 (c x c, ld c), so that S = M D_tau.
+int launch_wy_inverse(int64_t c, const double* Gm, const double* tau, double* M, cudaStream_t st);
 
 // Scratch of launch_small_svd (beside the dgemm scratch it also takes).
 size_t small_svd_scratch_bytes(int b);

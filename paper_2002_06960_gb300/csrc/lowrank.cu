@@ -161,45 +161,41 @@ __global__ void hqr_rev_gen(int r, int c, int j, double tau, double vv, double* 
 }
 
 // ------------------------------------------------------------ larft adjoint
-// Given W (r x c), tau, S = larft(W, tau), Gm = W^T W (c x c, ld c) and
-// Sb (c x c, ld c, upper part meaningful; consumed), add to taub and write
-// Gb (c x c) with the Gram adjoint (upper part; caller adds W (Gb + Gb^T)).
-__global__ void larft_rev_kernel(int c, const double* __restrict__ S, const double* __restrict__ Gm,
-                                 const double* __restrict__ tau, double* Sb, double* Gb,
-                                 double* taub) {
-  __shared__ double yb[256];
-  __shared__ double red[32];
-  for (int e = threadIdx.x; e < c * c; e += blockDim.x) Gb[e] = 0.0;
-  __syncthreads();
-  for (int j = c - 1; j >= 0; --j) {
-    const double tj = tau[j];
-    for (int i = threadIdx.x; i < j; i += blockDim.x) yb[i] = Sb[i + (int64_t)j * c];
-    __syncthreads();
-    // w = S(0:j,0:j) z, z = Gm(0:j, j);  taub_j += Sb(j,j) - yb . w
-    double part = 0.0;
-    for (int i = threadIdx.x; i < j; i += blockDim.x) {
-      double w = 0.0;
-      for (int l = i; l < j; ++l) w = fma(S[i + (int64_t)l * c], Gm[l + (int64_t)j * c], w);
-      part = fma(yb[i], w, part);
-    }
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = part;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
-      taub[j] += Sb[j + (int64_t)j * c] - s;
-    }
-    // Sb(0:j,0:j) += -tau_j yb z^T (upper part); zb = -tau_j S(0:j,0:j)^T yb -> Gb(0:j, j)
-    for (int l = threadIdx.x; l < j; l += blockDim.x) {
-      double zb = 0.0;
-      for (int i = 0; i <= l; ++i) zb = fma(S[i + (int64_t)l * c], yb[i], zb);
-      Gb[l + (int64_t)j * c] = -tj * zb;
-      const double z = Gm[l + (int64_t)j * c];
-      for (int i = 0; i <= l; ++i) Sb[i + (int64_t)l * c] += -tj * yb[i] * z;
-    }
-    __syncthreads();
+// Mb = triu(Sb) diag(tau)  (b x b, ld b)
+__global__ void larft_rev_scale_kernel(int c, const double* __restrict__ Sb,
+                                       const double* __restrict__ tau, double* __restrict__ Mb) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < c * c; e += gridDim.x * blockDim.x) {
+    const int i = e % c, j = e / c;
+    Mb[e] = (i <= j) ? Sb[e] * tau[j] : 0.0;
   }
+}
+
+// Row i (one warp): Gb(i, l) = tau_i Kb(i, l) for l > i (0 elsewhere in the row), and
+// taub_i += sum_j M(j, i) Sb(j, i) [j <= i] + sum_{l > i} Kb(i, l) Gm(i, l), each sum in a
+// fixed order (lane strides, then a shuffle tree).
+__global__ void larft_rev_finish_kernel(int c, const double* __restrict__ Kb,
+                                        const double* __restrict__ M,
+                                        const double* __restrict__ Sb,
+                                        const double* __restrict__ Gm,
+                                        const double* __restrict__ tau, double* __restrict__ Gb,
+                                        double* __restrict__ taub) {
+  const int i = blockIdx.x, lane = threadIdx.x;
+  const double ti = tau[i];
+  double acc = 0.0;
+  for (int l = lane; l < c; l += 32) {
+    const int64_t o = i + (int64_t)l * c;
+    const double kb = Kb[o];
+    if (l > i) {
+      Gb[o] = ti * kb;
+      acc = fma(kb, Gm[o], acc);
+    } else {
+      Gb[o] = 0.0;
+    }
+    // (M^T triu(Sb))_ii: column i of M and of Sb, rows l <= i
+    if (l <= i) acc = fma(M[l + (int64_t)i * c], Sb[l + (int64_t)i * c], acc);
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) taub[i] += acc;
 }
 
 __global__ void axpy_kernel(int64_t n, double a, const double* x, double* y) {
@@ -351,16 +347,34 @@ int left_apply_rev(LCtx& c, int64_t rows, int64_t cols, int64_t b, const double*
   return 0;
 }
 
-// S and tau adjoint (Sb consumed) -> taub += ..., Wb += W (Gb + Gb^T).
+// S and tau adjoint (Sb, upper part, consumed) -> taub += ..., Wb += W (Gb + Gb^T).
+// S = M D with M = (I + D N)^-1, D = diag(tau), N = striu(Gm): with Mb = triu(Sb) D and
+// Kb = -M^T Mb M^T, the Gram adjoint is striu(D Kb) and taub_i gets (M^T triu(Sb))_ii +
+// sum_{l > i} Kb_il N_il.  Four b x b products instead of a column-by-column walk in one
+// CTA.  ws: 4 b^2 doubles.
 int larft_reverse(LCtx& c, int64_t r, int64_t b, const double* W, const double* tau,
                   const double* S, const double* Gm, double* Sb, double* Wb, double* taub,
-                  double* Gb) {
+                  double* Gb, double* ws) {
+  (void)S;
+  double* M = ws;
+  double* Mb = M + b * b;
+  double* T1 = Mb + b * b;
+  double* Kb = T1 + b * b;
+  RUTV_TRY(launch_wy_inverse(b, Gm, tau, M, c.st));
   {
-    ProfScope prof(K_ADJOINT, (double)b * b * b, 32.0 * (double)b * b, c.st);
-    larft_rev_kernel<<<1, 256, 0, c.st>>>((int)b, S, Gm, tau, Sb, Gb, taub);
+    ProfScope prof(K_ADJOINT, 0.0, 24.0 * (double)b * b, c.st);
+    larft_rev_scale_kernel<<<grid_of(b * b), 256, 0, c.st>>>((int)b, Sb, tau, Mb);
+    note_launch();
+    RUTV_CK(cudaGetLastError());
   }
-  note_launch();
-  RUTV_CK(cudaGetLastError());
+  RUTV_TRY(G(c, false, true, b, b, b, 1.0, Mb, b, M, b, 0.0, T1, b));     // Mb M^T
+  RUTV_TRY(G(c, true, false, b, b, b, -1.0, M, b, T1, b, 0.0, Kb, b));    // -M^T Mb M^T
+  {
+    ProfScope prof(K_ADJOINT, 0.0, 32.0 * (double)b * b, c.st);
+    larft_rev_finish_kernel<<<(unsigned)b, 32, 0, c.st>>>((int)b, Kb, M, Sb, Gm, tau, Gb, taub);
+    note_launch();
+    RUTV_CK(cudaGetLastError());
+  }
   RUTV_TRY(G(c, false, false, r, b, b, 1.0, W, r, Gb, b, 1.0, Wb, r));
   RUTV_TRY(G(c, false, true, r, b, b, 1.0, W, r, Gb, b, 1.0, Wb, r));
   return 0;
@@ -568,13 +582,14 @@ int randutv_lowrank_backward(int64_t m, int64_t n, const double* A, int64_t lda,
   double* Wb = pool.get((size_t)big * b);
   double* Sb = pool.get((size_t)b * b);
   double* Gb = pool.get((size_t)b * b);
+  double* lws = pool.get((size_t)4 * b * b);  // larft_reverse workspace
   double* taub = pool.get(b);
   double* Pb = pool.get((size_t)big * b);
   double* Mb = pool.get((size_t)m * n);
   double* Nb = pool.get((size_t)m * n);
   double* Ob = pool.get((size_t)m * big);  // holds m x n and m x rm adjoints
-  if (!U || !ap || !Ub || !UtA || !t1 || !t2 || !t3 || !Wb || !Sb || !Gb || !taub || !Pb || !Mb ||
-      !Nb || !Ob)
+  if (!U || !ap || !Ub || !UtA || !t1 || !t2 || !t3 || !Wb || !Sb || !Gb || !lws || !taub || !Pb ||
+      !Mb || !Nb || !Ob)
     return RANDUTV_ENOMEM;
   std::vector<StepState> st;
   RUTV_TRY(lowrank_forward(c, pool, m, n, A, lda, k, b, q, seed, st, U, ap));
@@ -633,7 +648,7 @@ int randutv_lowrank_backward(int64_t m, int64_t n, const double* A, int64_t lda,
     RUTV_TRY(left_apply_rev(c, rm, nc, b, S.N + b * rm, rm, Ob, rm, S.WU, S.SU, Nb + b * rm, rm,
                             Wb, Sb, t1, t2, t3, S.WN));
     // ---- panel QR of N(:, 0:b)
-    RUTV_TRY(larft_reverse(c, rm, b, S.WU, S.tauU, S.SU, S.GU, Sb, Wb, taub, Gb));
+    RUTV_TRY(larft_reverse(c, rm, b, S.WU, S.tauU, S.SU, S.GU, Sb, Wb, taub, Gb, lws));
     keep_strict_lower<<<grid_of(rm * b), 256, 0, c.st>>>(rm, b, Wb);
     note_launch();
     RUTV_TRY(hqr_reverse(c, rm, b, S.PU, S.WU, S.tauU, Wb, taub, Pb, ap));
@@ -645,7 +660,7 @@ int randutv_lowrank_backward(int64_t m, int64_t n, const double* A, int64_t lda,
       RUTV_TRY(zero(c, taub, b));
       RUTV_TRY(right_apply_rev(c, rm, rn, b, S.M, rm, Nb, rm, S.WV, S.SV, Mb, rm, Wb, Sb, t1, t2,
                                t3, S.MW));
-      RUTV_TRY(larft_reverse(c, rn, b, S.WV, S.tauV, S.SV, S.GV, Sb, Wb, taub, Gb));
+      RUTV_TRY(larft_reverse(c, rn, b, S.WV, S.tauV, S.SV, S.GV, Sb, Wb, taub, Gb, lws));
       keep_strict_lower<<<grid_of(rn * b), 256, 0, c.st>>>(rn, b, Wb);
       note_launch();
       RUTV_TRY(hqr_reverse(c, rn, b, S.PV, S.WV, S.tauV, Wb, taub, Pb, ap));
