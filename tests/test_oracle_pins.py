@@ -231,6 +231,37 @@ def _check_svd(B, Us, D, Vs, tol=1e-14):
         assert float(col[idx]) > 0
 
 
+@pytest.mark.parametrize("zero_tau", [False, True])
+def test_wy_factor_adjoint_closed_form(zero_tau):
+    """The reverse of the WY factor that the backward form runs as b x b products: with
+    N = striu(W^T W), D = diag(tau), M = (I + D N)^-1 (so that S = M D), Mb = triu(Sb) D and
+    Kb = -M^T Mb M^T, the adjoints are Gb = striu(D Kb), Wb = W (Gb + Gb^T) and
+    tau_b = diag(M^T triu(Sb)) + rowsum(striu(Kb) * N).  Checked against autograd through the
+    oracle's column recurrence, also with identity reflectors (tau = 0)."""
+    g = torch.Generator().manual_seed(11)
+    r, c = 40, 12
+    W = torch.randn(r, c, generator=g, dtype=torch.float64)
+    tau = torch.rand(c, generator=g, dtype=torch.float64) + 0.5
+    if zero_tau:
+        tau[3] = 0.0
+        tau[8] = 0.0
+    Sb = torch.triu(torch.randn(c, c, generator=g, dtype=torch.float64))
+    Wv = W.clone().requires_grad_(True)
+    tv = tau.clone().requires_grad_(True)
+    (oracle.wy_factor(Wv, tv) * Sb).sum().backward()
+    N = torch.triu(W.T @ W, 1)
+    D = torch.diag(tau)
+    M = torch.linalg.inv(torch.eye(c, dtype=torch.float64) + D @ N)
+    assert torch.allclose(M @ D, oracle.wy_factor(W, tau), atol=1e-13)
+    Kb = -M.T @ (Sb @ D) @ M.T
+    Gb = torch.triu(D @ Kb, 1)
+    Wb = W @ (Gb + Gb.T)
+    taub = torch.diag(M.T @ Sb) + (torch.triu(Kb, 1) * N).sum(1)
+    scale = float(Wv.grad.abs().max())
+    assert float((Wb - Wv.grad).abs().max()) <= 1e-12 * scale
+    assert float((taub - tv.grad).abs().max()) <= 1e-12 * max(1.0, float(tv.grad.abs().max()))
+
+
 def test_small_svd_diagonal_closed_form():
     B = torch.diag(torch.tensor([3.0, -1.0, 2.0, 0.5], dtype=f64))
     Us, D, Vs = oracle.small_svd(B)
